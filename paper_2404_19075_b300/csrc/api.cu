@@ -1,0 +1,585 @@
+// C ABI of libdinr (include/dinr.h): context management, argument checks,
+// and dispatch to the step / query pipelines.
+#include "context.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace dinr;
+
+static char g_create_error[512] = "no error";
+
+int dinr_fail(dinr_ctx *c, int status, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) {
+    snprintf(c->err, sizeof(c->err), "%s", buf);
+    if (status == DINR_ERR_CUDA) c->failed = true;
+  } else {
+    snprintf(g_create_error, sizeof(g_create_error), "%s", buf);
+  }
+  return status;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "%s: %s (%s:%d)", #call,        \
+                                    cudaGetErrorString(e_), __FILE__, __LINE__);      \
+  } while (0)
+#define CKL() CK(cudaGetLastError())
+#define LIVE(c)                                                                       \
+  do {                                                                                \
+    if (!(c)) return DINR_ERR_ARG;                                                    \
+    if ((c)->failed) return DINR_ERR_CUDA;                                            \
+  } while (0)
+
+// ------------------------------------------------------------ helpers
+
+int64_t dinr_param_count(int n_freq, int hidden_layers, int width) {
+  if (n_freq < 0 || hidden_layers < 1 || width < 1) return -1;
+  int64_t d_in = 4 + 8 * (int64_t)n_freq, W = width;
+  return W * d_in + W + (int64_t)(hidden_layers - 1) * (W * W + W) + W + 1;
+}
+
+// He initialisation: SplitMix64 stream of `seed`, Box-Muller pairs (u1 from
+// (0,1]); weight entries in layout order take consecutive normals scaled by
+// sqrt(2/fan_in); biases are 0.
+static void he_init_host(const dinr_ctx *c, uint64_t seed, std::vector<float> &out) {
+  out.assign(c->P, 0.0f);
+  uint64_t k = 0;
+  auto uni = [&]() {
+    ++k;
+    return (double)(mix64(seed + k * kGamma) >> 11) * (1.0 / 9007199254740992.0);
+  };
+  double spare = 0.0;
+  bool have = false;
+  auto normal = [&]() {
+    if (have) {
+      have = false;
+      return spare;
+    }
+    double u1 = 1.0 - uni(), u2 = uni();
+    double r = std::sqrt(-2.0 * std::log(u1));
+    spare = r * std::sin(2.0 * M_PI * u2);
+    have = true;
+    return r * std::cos(2.0 * M_PI * u2);
+  };
+  for (int L = 0; L <= c->H; ++L) {
+    int64_t fo = c->fan_out[L], fi = c->fan_in[L];
+    double sd = std::sqrt(2.0 / (double)fi);
+    for (int64_t q = 0; q < fo * fi; ++q) out[c->offW[L] + q] = (float)(normal() * sd);
+  }
+}
+
+static void *dev_alloc(dinr_ctx *c, size_t bytes, bool *ok) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ok = false;
+    return nullptr;
+  }
+  c->allocs.push_back(p);
+  return p;
+}
+
+static int check_geometry(const dinr_geometry *g) {
+  if (!g || !g->view_angle || !g->view_time) return 0;
+  if (g->beam != DINR_BEAM_PARALLEL && g->beam != DINR_BEAM_CONE) return 0;
+  if (g->n_views < 1 || g->det_rows < 1 || g->det_cols < 1) return 0;
+  if (!(g->det_pitch_u > 0) || !(g->det_pitch_v > 0) || !(g->fov_r > 0)) return 0;
+  if (!(g->fov_z1 > g->fov_z0) || !(g->t1 > g->t0)) return 0;
+  if (g->samples_per_ray < 1 || g->samples_per_ray > 4096) return 0;
+  if (g->beam == DINR_BEAM_CONE && (!(g->sod > g->fov_r) || !(g->sdd > g->sod))) return 0;
+  return 1;
+}
+
+// Device geometry tables from the host description (FP64, per view).
+static dinr_status setup_geometry(dinr_ctx *c, const dinr_geometry *g, GeoDev *geo,
+                                  double2 **cs_out, double **tbar_out, double **t_out,
+                                  cudaStream_t st) {
+  int M = g->n_views;
+  std::vector<double2> cs(M);
+  std::vector<double> tb(M), tt(M);
+  for (int m = 0; m < M; ++m) {
+    cs[m] = make_double2(std::cos(g->view_angle[m]), std::sin(g->view_angle[m]));
+    tt[m] = g->view_time[m];
+    tb[m] = 2.0 * (g->view_time[m] - g->t0) / (g->t1 - g->t0) - 1.0;
+  }
+  bool ok = true;
+  *cs_out = (double2 *)dev_alloc(c, sizeof(double2) * M, &ok);
+  *tbar_out = (double *)dev_alloc(c, sizeof(double) * M, &ok);
+  *t_out = (double *)dev_alloc(c, sizeof(double) * M, &ok);
+  if (!ok) return (dinr_status)dinr_fail(c, DINR_ERR_OOM, "geometry tables: out of memory");
+  CK(cudaMemcpyAsync(*cs_out, cs.data(), sizeof(double2) * M, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(*tbar_out, tb.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(*t_out, tt.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  GeoDev &d = *geo;
+  d.beam = g->beam;
+  d.n_views = g->n_views;
+  d.det_rows = g->det_rows;
+  d.det_cols = g->det_cols;
+  d.n_pixels = (long long)g->det_rows * g->det_cols;
+  d.n_proj = d.n_pixels * g->n_views;
+  d.pu = g->det_pitch_u;
+  d.pv = g->det_pitch_v;
+  d.ou = g->det_off_u;
+  d.ov = g->det_off_v;
+  d.sod = g->sod;
+  d.sdd = g->sdd;
+  d.R = g->fov_r;
+  d.z0 = g->fov_z0;
+  d.z1 = g->fov_z1;
+  d.inv_R = 1.0 / g->fov_r;
+  d.zs = 2.0 / (g->fov_z1 - g->fov_z0);
+  d.zb = -(g->fov_z0 + g->fov_z1) / (g->fov_z1 - g->fov_z0);
+  d.S = g->samples_per_ray;
+  d.mu0 = (float)g->mu0;
+  d.view_cs = *cs_out;
+  d.view_tbar = *tbar_out;
+  return DINR_OK;
+}
+
+// ------------------------------------------------------------- create
+
+static dinr_status create_fail(dinr_ctx *c, dinr_status s) {
+  if (c) {
+    snprintf(g_create_error, sizeof(g_create_error), "%s", c->err);
+    dinr_destroy(c);
+  }
+  return s;
+}
+
+dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const dinr_train *train,
+                        const float *proj, int proj_on_device, void *cuda_stream,
+                        dinr_ctx **out) {
+  if (!out) return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!check_geometry(geom))
+    return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid geometry");
+  if (!net || net->n_freq < 0 || net->n_freq > kMaxFreq || net->hidden_layers < 1 ||
+      net->hidden_layers > 32 || net->width < 1 || net->width > 1024 ||
+      (net->act != DINR_ACT_RELU && net->act != DINR_ACT_SWISH) ||
+      (net->out_act != DINR_OUT_IDENTITY && net->out_act != DINR_OUT_SOFTPLUS))
+    return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid network shape");
+  if (net->prec != DINR_PREC_FP32 && net->prec != DINR_PREC_BF16)
+    return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid precision");
+  if (!train || train->batch_rays < 1 || train->chunk_rays < 0)
+    return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid training options");
+  if (!proj) return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "proj is NULL");
+  if (net->prec == DINR_PREC_BF16 && !bf16_supported(net))
+    return (dinr_status)dinr_fail(nullptr, DINR_ERR_UNSUPPORTED,
+                                  "the BF16 path does not support this network shape");
+
+  dinr_ctx *c = new (std::nothrow) dinr_ctx();
+  if (!c) return (dinr_status)dinr_fail(nullptr, DINR_ERR_OOM, "host allocation failed");
+  c->st = (cudaStream_t)cuda_stream;
+  cudaStream_t st = c->st;
+  c->F = net->n_freq;
+  c->H = net->hidden_layers;
+  c->W = net->width;
+  c->act = net->act;
+  c->out_act = net->out_act;
+  c->prec = net->prec;
+  c->d_in = 4 + 8 * c->F;
+  c->ldE = (c->d_in + 15) / 16 * 16;
+  c->S = geom->samples_per_ray;
+  c->mu0 = (float)geom->mu0;
+  c->det_rows = geom->det_rows;
+  c->det_cols = geom->det_cols;
+  c->t0 = geom->t0;
+  c->t1 = geom->t1;
+  long long off = 0;
+  for (int L = 0; L <= c->H; ++L) {
+    int fi = L == 0 ? c->d_in : c->W, fo = L == c->H ? 1 : c->W;
+    c->fan_in.push_back(fi);
+    c->fan_out.push_back(fo);
+    c->offW.push_back(off);
+    off += (long long)fi * fo;
+    c->offb.push_back(off);
+    off += fo;
+  }
+  c->P = off;
+  c->lr = train->lr > 0 ? train->lr : 1e-3;
+  c->b1 = train->beta1 > 0 ? train->beta1 : 0.9;
+  c->b2 = train->beta2 > 0 ? train->beta2 : 0.999;
+  c->eps = train->eps > 0 ? train->eps : 1e-8;
+  c->decay = train->lr_decay_per_epoch > 0 ? train->lr_decay_per_epoch : 1.0;
+  c->batch_rays = train->batch_rays;
+  c->sampler_seed = train->sampler_seed;
+
+  dinr_status s = setup_geometry(c, geom, &c->geo, &c->d_view_cs, &c->d_view_tbar,
+                                 &c->d_view_t, st);
+  if (s != DINR_OK) return create_fail(c, s);
+  c->n_proj = c->geo.n_proj;
+
+  bool ok = true;
+  c->d_params = (float *)dev_alloc(c, sizeof(float) * c->P, &ok);
+  c->d_m = (float *)dev_alloc(c, sizeof(float) * c->P, &ok);
+  c->d_v = (float *)dev_alloc(c, sizeof(float) * c->P, &ok);
+  c->d_grad = (float *)dev_alloc(c, sizeof(float) * c->P, &ok);
+  c->d_loss = (float *)dev_alloc(c, sizeof(float) * 4, &ok);
+  c->d_proj = (float *)dev_alloc(c, sizeof(float) * c->n_proj, &ok);
+  c->d_idx = (long long *)dev_alloc(c, sizeof(long long) * c->batch_rays, &ok);
+  c->d_flag = (int *)dev_alloc(c, sizeof(int) * 4, &ok);
+  if (!ok) {
+    dinr_fail(c, DINR_ERR_OOM, "device allocation of parameters/projections failed");
+    return create_fail(c, DINR_ERR_OOM);
+  }
+  std::vector<float> init;
+  const float *src = net->init_params;
+  if (!src) {
+    he_init_host(c, net->seed, init);
+    src = init.data();
+  }
+  CK(cudaMemcpyAsync(c->d_params, src, sizeof(float) * c->P, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(c->d_m, 0, sizeof(float) * c->P, st));
+  CK(cudaMemsetAsync(c->d_v, 0, sizeof(float) * c->P, st));
+  CK(cudaMemsetAsync(c->d_grad, 0, sizeof(float) * c->P, st));
+  CK(cudaMemsetAsync(c->d_loss, 0, sizeof(float) * 4, st));
+  CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int) * 4, st));
+  CK(cudaMemcpyAsync(c->d_proj, proj, sizeof(float) * c->n_proj,
+                     proj_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+
+  // Rays per pass: bounded so that the activations of a pass fit in a
+  // workspace budget of 60 % of free memory, at most 96 GiB.
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  long long per_sample = workspace_bytes_per_sample(c);
+  long long budget = (long long)(free_b * 0.6);
+  if (budget > (96LL << 30)) budget = 96LL << 30;
+  long long max_rays = budget / (per_sample * c->S + 64);
+  long long chunk = train->chunk_rays > 0 ? train->chunk_rays : c->batch_rays;
+  if (chunk > c->batch_rays) chunk = c->batch_rays;
+  if (chunk > max_rays) chunk = max_rays;
+  if (chunk < 1) {
+    dinr_fail(c, DINR_ERR_OOM, "not enough device memory for one ray");
+    return create_fail(c, DINR_ERR_OOM);
+  }
+  c->chunk_rays = (int)chunk;
+  s = alloc_workspace(c);
+  if (s != DINR_OK) return create_fail(c, s);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    dinr_fail(c, DINR_ERR_CUDA, "create: %s", cudaGetErrorString(e));
+    return create_fail(c, DINR_ERR_CUDA);
+  }
+  *out = c;
+  return DINR_OK;
+}
+
+void dinr_destroy(dinr_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  destroy_backend(c);
+  for (void *p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+const char *dinr_last_error(const dinr_ctx *c) { return c ? c->err : g_create_error; }
+
+dinr_status dinr_synchronize(dinr_ctx *c) {
+  LIVE(c);
+  CK(cudaStreamSynchronize(c->st));
+  return DINR_OK;
+}
+
+dinr_status dinr_set_projections(dinr_ctx *c, const float *proj, int on_device) {
+  LIVE(c);
+  if (!proj) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "proj is NULL");
+  CK(cudaMemcpyAsync(c->d_proj, proj, sizeof(float) * c->n_proj,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+  return DINR_OK;
+}
+
+// Stage the minibatch indices into the context (sampler, host or device).
+static dinr_status stage_indices(dinr_ctx *c, const int64_t *idx, int n, int on_device) {
+  if (n < 1 || n > c->batch_rays)
+    return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "n = %d outside [1, %d]", n, c->batch_rays);
+  if (!idx) {
+    launch_sample_indices(c->n_proj, n, c->step, c->sampler_seed, c->d_idx, c->st);
+    CKL();
+  } else if (!on_device) {
+    for (int i = 0; i < n; ++i)
+      if (idx[i] < 0 || idx[i] >= c->n_proj)
+        return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "ray index %lld outside [0, %lld)",
+                                      (long long)idx[i], c->n_proj);
+    CK(cudaMemcpyAsync(c->d_idx, idx, sizeof(long long) * n, cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  } else {
+    CK(cudaMemcpyAsync(c->d_idx, idx, sizeof(long long) * n, cudaMemcpyDeviceToDevice, c->st));
+    // Out-of-range device indices are replaced by 0 and flagged, so that no
+    // kernel reads outside the view tables or the projection stack.
+    launch_check_indices(c->d_idx, n, c->n_proj, c->d_flag, c->st);
+    CKL();
+  }
+  return DINR_OK;
+}
+
+static dinr_status check_flag(dinr_ctx *c) {
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (bad) {
+    CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
+    return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "a device ray index was outside [0, M*N)");
+  }
+  return DINR_OK;
+}
+
+dinr_status dinr_loss_grad(dinr_ctx *c, const int64_t *idx, int n, int on_device,
+                           float *loss_dev, float *grad_dev) {
+  LIVE(c);
+  dinr_status s = stage_indices(c, idx, n, on_device);
+  if (s != DINR_OK) return s;
+  s = run_loss_grad(c, n);
+  if (s != DINR_OK) return s;
+  if (loss_dev)
+    CK(cudaMemcpyAsync(loss_dev, c->d_loss, sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+  if (grad_dev)
+    CK(cudaMemcpyAsync(grad_dev, c->d_grad, sizeof(float) * c->P, cudaMemcpyDeviceToDevice,
+                       c->st));
+  return DINR_OK;
+}
+
+dinr_status dinr_train_step(dinr_ctx *c, const int64_t *idx, int n, int on_device,
+                            float *loss_out) {
+  LIVE(c);
+  dinr_status s = stage_indices(c, idx, n, on_device);
+  if (s != DINR_OK) return s;
+  s = run_loss_grad(c, n);
+  if (s != DINR_OK) return s;
+  // Adam step t = step + 1 with bias corrections and the epoch's learning rate.
+  long long t = c->step + 1;
+  long long spe = (c->n_proj + n - 1) / n;
+  double lr = c->lr * std::pow(c->decay, (double)(c->step / spe));
+  double bc1 = 1.0 / (1.0 - std::pow(c->b1, (double)t));
+  double bc2 = 1.0 / (1.0 - std::pow(c->b2, (double)t));
+  launch_adam(c->d_params, c->d_m, c->d_v, c->d_grad, c->P, (float)lr, (float)c->b1,
+              (float)c->b2, (float)c->eps, (float)bc1, (float)bc2, c->st);
+  CKL();
+  s = after_param_update(c);
+  if (s != DINR_OK) return s;
+  c->step = t;
+  if (idx && on_device && loss_out) {
+    s = check_flag(c);
+    if (s != DINR_OK) return s;
+  }
+  if (loss_out) {
+    CK(cudaMemcpyAsync(loss_out, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (!std::isfinite(*loss_out))
+      return (dinr_status)dinr_fail(c, DINR_ERR_NONFINITE, "loss is not finite");
+  }
+  return DINR_OK;
+}
+
+dinr_status dinr_predict(dinr_ctx *c, const int64_t *idx, int n, int on_device, float *pbar) {
+  LIVE(c);
+  if (!pbar) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "pbar is NULL");
+  dinr_status s = stage_indices(c, idx, n, on_device);
+  if (s != DINR_OK) return s;
+  SourceArgs src{};
+  src.kind = kSrcTrainRays;
+  src.idx = c->d_idx;
+  return run_forward_rays(c, src, n, c->S, pbar);
+}
+
+dinr_status dinr_project(dinr_ctx *c, double theta, double t, int rows, int cols, int S,
+                         float *out) {
+  LIVE(c);
+  if (!out || rows < 1 || cols < 1 || S < 1 || S > 4096 ||
+      (long long)rows * cols * S > (1LL << 31))
+    return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "invalid projection request");
+  SourceArgs src{};
+  src.kind = kSrcVirtualView;
+  src.vc = std::cos(theta);
+  src.vs = std::sin(theta);
+  src.vtbar = 2.0 * (t - c->t0) / (c->t1 - c->t0) - 1.0;
+  src.vpu = c->geo.pu * c->det_cols / cols;
+  src.vpv = c->geo.pv * c->det_rows / rows;
+  src.vrows = rows;
+  src.vcols = cols;
+  return run_forward_rays(c, src, (long long)rows * cols, S, out);
+}
+
+dinr_status dinr_query(dinr_ctx *c, const float *coords, int64_t n, float *out) {
+  LIVE(c);
+  if (!coords || !out || n < 0) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "invalid query");
+  if (n == 0) return DINR_OK;
+  SourceArgs src{};
+  src.kind = kSrcPoints;
+  src.points = coords;
+  src.t_scale = 2.0 / (c->t1 - c->t0);
+  src.t_bias = -2.0 * c->t0 / (c->t1 - c->t0) - 1.0;
+  return run_forward_points(c, src, n, out);
+}
+
+dinr_status dinr_query_grid(dinr_ctx *c, double t, const double *lo, const double *hi,
+                            const int *dims, float *out) {
+  LIVE(c);
+  if (!lo || !hi || !dims || !out || dims[0] < 1 || dims[1] < 1 || dims[2] < 1)
+    return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "invalid grid query");
+  SourceArgs src{};
+  src.kind = kSrcGrid;
+  for (int d = 0; d < 3; ++d) {
+    src.glo[d] = lo[d];
+    src.gstep[d] = (hi[d] - lo[d]) / dims[d];
+    src.gdims[d] = dims[d];
+  }
+  src.gtbar = 2.0 * (t - c->t0) / (c->t1 - c->t0) - 1.0;
+  long long n = (long long)dims[0] * dims[1] * dims[2];
+  return run_forward_points(c, src, n, out);
+}
+
+dinr_status dinr_set_params(dinr_ctx *c, const float *p, int on_device) {
+  LIVE(c);
+  if (!p) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "params is NULL");
+  CK(cudaMemcpyAsync(c->d_params, p, sizeof(float) * c->P,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+  return after_param_update(c);
+}
+
+dinr_status dinr_get_params(dinr_ctx *c, float *p, int on_device) {
+  LIVE(c);
+  if (!p) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "params is NULL");
+  CK(cudaMemcpyAsync(p, c->d_params, sizeof(float) * c->P,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  if (!on_device) CK(cudaStreamSynchronize(c->st));
+  return DINR_OK;
+}
+
+dinr_status dinr_get_grads(dinr_ctx *c, float *host) {
+  LIVE(c);
+  if (!host) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "host is NULL");
+  CK(cudaMemcpyAsync(host, c->d_grad, sizeof(float) * c->P, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return DINR_OK;
+}
+
+dinr_status dinr_get_loss(dinr_ctx *c, float *host) {
+  LIVE(c);
+  if (!host) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "host is NULL");
+  CK(cudaMemcpyAsync(host, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return DINR_OK;
+}
+
+// ------------------------------------------------------------ state blob
+struct StateHeader {
+  char magic[8];
+  int32_t version, F, H, W;
+  int64_t P, step;
+  uint64_t sampler_seed;
+};
+
+dinr_status dinr_get_state(dinr_ctx *c, void *buf, size_t *bytes) {
+  LIVE(c);
+  if (!bytes) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "bytes is NULL");
+  size_t need = sizeof(StateHeader) + 3 * sizeof(float) * c->P;
+  if (!buf) {
+    *bytes = need;
+    return DINR_OK;
+  }
+  if (*bytes < need) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "buffer too small");
+  StateHeader h{};
+  memcpy(h.magic, "DINRST1", 8);
+  h.version = 1;
+  h.F = c->F;
+  h.H = c->H;
+  h.W = c->W;
+  h.P = c->P;
+  h.step = c->step;
+  h.sampler_seed = c->sampler_seed;
+  char *b = (char *)buf;
+  memcpy(b, &h, sizeof(h));
+  float *f = (float *)(b + sizeof(h));
+  CK(cudaMemcpyAsync(f, c->d_params, sizeof(float) * c->P, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(f + c->P, c->d_m, sizeof(float) * c->P, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(f + 2 * c->P, c->d_v, sizeof(float) * c->P, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *bytes = need;
+  return DINR_OK;
+}
+
+dinr_status dinr_set_state(dinr_ctx *c, const void *buf, size_t bytes) {
+  LIVE(c);
+  size_t need = sizeof(StateHeader) + 3 * sizeof(float) * c->P;
+  if (!buf || bytes != need)
+    return (dinr_status)dinr_fail(c, DINR_ERR_STATE, "state size mismatch");
+  StateHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (memcmp(h.magic, "DINRST1", 8) != 0 || h.version != 1 || h.F != c->F || h.H != c->H ||
+      h.W != c->W || h.P != c->P)
+    return (dinr_status)dinr_fail(c, DINR_ERR_STATE, "state does not match this network");
+  const float *f = (const float *)((const char *)buf + sizeof(h));
+  CK(cudaMemcpyAsync(c->d_params, f, sizeof(float) * c->P, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->d_m, f + c->P, sizeof(float) * c->P, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->d_v, f + 2 * c->P, sizeof(float) * c->P, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->step = h.step;
+  c->sampler_seed = h.sampler_seed;
+  return after_param_update(c);
+}
+
+dinr_status dinr_sample_indices(dinr_ctx *c, int64_t step, int n, int64_t *out) {
+  LIVE(c);
+  if (!out || n < 1 || step < 0)
+    return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "invalid sampler request");
+  launch_sample_indices(c->n_proj, n, step, c->sampler_seed, (long long *)out, c->st);
+  CKL();
+  return DINR_OK;
+}
+
+// ------------------------------------------------------- phantom utility
+dinr_status dinr_phantom_project(const dinr_geometry *geom, int n_ell, const double *centre,
+                                 const double *axes, const double *rho, const double *vel,
+                                 double growth, const int64_t *idx, int64_t n, float *out,
+                                 void *cuda_stream) {
+  if (!check_geometry(geom) || n_ell < 0 || (n_ell > 0 && (!centre || !axes || !rho)) ||
+      !out || n < 0)
+    return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid phantom request");
+  dinr_ctx tmp;  // holds the temporary allocations and the message
+  dinr_ctx *c = &tmp;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  GeoDev g{};
+  double2 *cs = nullptr;
+  double *tb = nullptr, *tt = nullptr;
+  dinr_status s = setup_geometry(c, geom, &g, &cs, &tb, &tt, st);
+  if (s == DINR_OK && n > 0) {
+    std::vector<double> ell(10 * (size_t)(n_ell > 0 ? n_ell : 1), 0.0);
+    for (int k = 0; k < n_ell; ++k) {
+      for (int d = 0; d < 3; ++d) {
+        ell[10 * k + d] = centre[3 * k + d];
+        ell[10 * k + 3 + d] = axes[3 * k + d];
+        ell[10 * k + 7 + d] = vel ? vel[3 * k + d] : 0.0;
+      }
+      ell[10 * k + 6] = rho[k];
+    }
+    bool ok = true;
+    double *d_ell = (double *)dev_alloc(c, sizeof(double) * ell.size(), &ok);
+    if (!ok) {
+      s = DINR_ERR_OOM;
+    } else if (cudaMemcpyAsync(d_ell, ell.data(), sizeof(double) * ell.size(),
+                               cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      s = DINR_ERR_CUDA;
+    } else {
+      launch_phantom(g, tt, n_ell, d_ell, growth, (const long long *)idx, n, out, st);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        s = DINR_ERR_CUDA;
+    }
+  }
+  if (s != DINR_OK) dinr_fail(nullptr, s, "phantom projection failed (%s)", tmp.err);
+  for (void *p : tmp.allocs) cudaFree(p);
+  return s;
+}

@@ -1,0 +1,66 @@
+// The context behind the opaque dinr_ctx handle, and the pipeline entry
+// points the C ABI dispatches to.
+#pragma once
+
+#include "../../include/dinr.h"
+#include "internal.cuh"
+
+#include <vector>
+
+struct dinr_ctx {
+  cudaStream_t st = nullptr;
+  dinr::GeoDev geo{};
+  double2 *d_view_cs = nullptr;
+  double *d_view_tbar = nullptr, *d_view_t = nullptr;
+  double t0 = 0, t1 = 1;
+  int det_rows = 0, det_cols = 0, S = 1;
+  float mu0 = 1.0f;
+
+  // network: layer L = 0..H-1 hidden, L = H output; offsets into the flat vector
+  int F = 0, H = 0, W = 0, act = 0, out_act = 0, prec = 0, d_in = 0, ldE = 0;
+  long long P = 0;
+  std::vector<int> fan_in, fan_out;
+  std::vector<long long> offW, offb;
+
+  float *d_params = nullptr, *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr;
+  float *d_loss = nullptr, *d_proj = nullptr;
+  long long n_proj = 0;
+  long long *d_idx = nullptr;
+  int *d_flag = nullptr;
+
+  double lr = 1e-3, b1 = 0.9, b2 = 0.999, eps = 1e-8, decay = 1.0;
+  int batch_rays = 0, chunk_rays = 0;
+  uint64_t sampler_seed = 0;
+  long long step = 0;  // completed Adam steps
+
+  // FP32 workspace (per pass of chunk_rays rays)
+  float *E = nullptr, *Z = nullptr, *D0 = nullptr, *D1 = nullptr;
+  float *zout = nullptr, *dz = nullptr;
+  float *ray_l = nullptr, *ray_p = nullptr, *pbar = nullptr, *sq = nullptr;
+  float *part = nullptr;
+  long long part_floats = 0;
+
+  // BF16 (tensor-core) backend state, owned by the tensor-core pipeline.
+  void *tc = nullptr;
+
+  char err[512] = "no error";
+  bool failed = false;
+  std::vector<void *> allocs;
+};
+
+int dinr_fail(dinr_ctx *c, int status, const char *fmt, ...);
+
+// Pipeline (pipeline.cu)
+bool bf16_supported(const dinr_net *net);
+long long workspace_bytes_per_sample(const dinr_ctx *c);
+dinr_status alloc_workspace(dinr_ctx *c);
+void destroy_backend(dinr_ctx *c);
+// Loss into d_loss and gradient into d_grad for the n staged rays in d_idx.
+dinr_status run_loss_grad(dinr_ctx *c, int n);
+// Forward model p_bar for n_rays rays of a source, S samples each, into out.
+dinr_status run_forward_rays(dinr_ctx *c, const dinr::SourceArgs &src, long long n_rays, int S,
+                             float *out);
+// mu0 * M at n points of a source into out.
+dinr_status run_forward_points(dinr_ctx *c, const dinr::SourceArgs &src, long long n, float *out);
+// Refresh derived copies of the parameters (BF16 weights) after a change.
+dinr_status after_param_update(dinr_ctx *c);

@@ -1,0 +1,364 @@
+// Non-GEMM kernels of libdinr: minibatch sampler, phantom projector, ray
+// generation + Fourier encoding, output layer + forward model + loss,
+// column sums, ordered reductions and Adam.
+#include "internal.cuh"
+
+namespace dinr {
+
+// ----------------------------------------------------------------- sampler
+// Keyed Feistel bijection of [0, 2^(2h)) with cycle walking into [0, n)
+// (Sec. III draws random pixel subsets; this is the library's construction).
+__device__ __forceinline__ uint64_t feistel(uint64_t x, const uint64_t *key, int h) {
+  uint64_t mask = (1ULL << h) - 1ULL;
+  uint64_t L = x >> h, R = x & mask;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    uint64_t nl = R;
+    R = L ^ (mix64(R ^ key[r]) & mask);
+    L = nl;
+  }
+  return (L << h) | R;
+}
+
+__global__ void k_sample(long long n, int B, long long step, uint64_t seed, int h,
+                         long long *out) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  long long spe = (n + B - 1) / B;
+  long long e = step / spe, j = step - e * spe;
+  uint64_t key[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) key[r] = mix64(seed + (uint64_t)(4 * e + r + 1) * kGamma);
+  uint64_t x = (uint64_t)((j * (long long)B + b) % n);
+  uint64_t y = feistel(x, key, h);
+  // Cycle walking ends: x < n lies on the cycle of a bijection.
+  while (y >= (uint64_t)n) y = feistel(y, key, h);
+  out[b] = (long long)y;
+}
+
+void launch_sample_indices(long long n, int B, long long step, uint64_t seed, long long *out,
+                           cudaStream_t st) {
+  int bits = 2;
+  while ((1LL << bits) < n) ++bits;
+  int h = (bits + 1) / 2;
+  k_sample<<<ceil_div(B, 256), 256, 0, st>>>(n, B, step, seed, h, out);
+}
+
+__global__ void k_check_indices(long long *idx, int n, long long n_proj, int *bad) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (idx[i] < 0 || idx[i] >= n_proj)) {
+    idx[i] = 0;
+    atomicExch(bad, 1);
+  }
+}
+void launch_check_indices(long long *idx, int n, long long n_proj, int *bad, cudaStream_t st) {
+  k_check_indices<<<ceil_div(n, 256), 256, 0, st>>>(idx, n, n_proj, bad);
+}
+
+// ----------------------------------------------------------------- phantom
+// ell: per ellipsoid 10 doubles: centre(3), axes(3), rho, vel(3).
+__global__ void k_phantom(GeoDev g, const double *view_t, int n_ell, const double *ell,
+                          double growth, const long long *idx, long long n, float *out) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  long long i = idx ? idx[q] : q;
+  if (i < 0 || i >= g.n_proj) {
+    out[q] = 0.0f;
+    return;
+  }
+  Ray r = make_ray(g, i);
+  double t = view_t[i / g.n_pixels];
+  double s1 = r.s0 + r.l, acc = 0.0;
+  if (r.l > 0.0) {
+    for (int k = 0; k < n_ell; ++k) {
+      const double *e = ell + 10 * k;
+      double f = 1.0 + growth * t;
+      double qx = (r.ox - e[0] - e[7] * t) / (e[3] * f);
+      double qy = (r.oy - e[1] - e[8] * t) / (e[4] * f);
+      double qz = (r.oz - e[2] - e[9] * t) / (e[5] * f);
+      double rx = r.dx / (e[3] * f), ry = r.dy / (e[4] * f), rz = r.dz / (e[5] * f);
+      double A = rx * rx + ry * ry + rz * rz;
+      double B = 2.0 * (qx * rx + qy * ry + qz * rz);
+      double C = qx * qx + qy * qy + qz * qz - 1.0;
+      double disc = B * B - 4.0 * A * C;
+      if (disc <= 0.0) continue;
+      double sq = sqrt(disc);
+      double lo = fmax((-B - sq) / (2.0 * A), r.s0);
+      double hi = fmin((-B + sq) / (2.0 * A), s1);
+      if (hi > lo) acc += e[6] * (hi - lo);
+    }
+  }
+  out[q] = (float)acc;
+}
+
+void launch_phantom(const GeoDev &g, const double *view_t, int n_ell, const double *ell,
+                    double growth, const long long *idx, long long n, float *out,
+                    cudaStream_t st) {
+  k_phantom<<<ceil_div(n, 128), 128, 0, st>>>(g, view_t, n_ell, ell, growth, idx, n, out);
+}
+
+// ---------------------------------------------------- rays and encoding
+// The ray of ray slot r for each ray source kind.
+__device__ __forceinline__ Ray source_ray(const GeoDev &g, const SourceArgs &s, long long r) {
+  if (s.kind == kSrcTrainRays) return make_ray(g, s.idx[r]);
+  long long q = s.first + r;
+  int row = (int)(q / s.vcols), col = (int)(q - (long long)row * s.vcols);
+  double u = g.ou + (col + 0.5) * s.vpu, v = g.ov + (row + 0.5) * s.vpv;
+  return ray_at(g, u, v, s.vc, s.vs, s.vtbar);
+}
+
+// Normalised (t, z, y, x) of sample j of ray/point slot r.
+__device__ __forceinline__ void source_coords(const GeoDev &g, const SourceArgs &s,
+                                              long long r, int j, double c[4], float *len) {
+  if (s.kind == kSrcTrainRays || s.kind == kSrcVirtualView) {
+    Ray ray = source_ray(g, s, r);
+    c[0] = ray.tbar;
+    sample_coords(g, ray, j, c[1], c[2], c[3]);
+    *len = (float)ray.l;
+  } else if (s.kind == kSrcPoints) {
+    const float *p = s.points + 4 * (s.first + r);
+    c[0] = (double)p[0] * s.t_scale + s.t_bias;
+    c[1] = (double)p[1] * g.zs + g.zb;
+    c[2] = (double)p[2] * g.inv_R;
+    c[3] = (double)p[3] * g.inv_R;
+    *len = 1.0f;
+  } else {
+    long long nx = s.gdims[0], ny = s.gdims[1], q = s.first + r;
+    long long iz = q / (nx * ny), rem = q - iz * nx * ny;
+    long long iy = rem / nx, ix = rem - iy * nx;
+    double x = s.glo[0] + (ix + 0.5) * s.gstep[0];
+    double y = s.glo[1] + (iy + 0.5) * s.gstep[1];
+    double z = s.glo[2] + (iz + 0.5) * s.gstep[2];
+    c[0] = s.gtbar;
+    c[1] = z * g.zs + g.zb;
+    c[2] = y * g.inv_R;
+    c[3] = x * g.inv_R;
+    *len = 1.0f;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T to_t(float x);
+template <>
+__device__ __forceinline__ float to_t<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_t<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+
+// One thread per sample. ray_l receives the chord length of each ray (1 for
+// point sources, so that the forward model reduces to mu0 * M); ray_p the
+// measured projection of each training ray.
+template <typename T>
+__global__ void k_encode(GeoDev g, SourceArgs src, long long n_rays, int S, int F, int ld,
+                         T *E, float *ray_l, const float *proj, float *ray_p) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n_rays * S) return;
+  long long r = q / S;
+  int j = (int)(q - r * S);
+  double c[4];
+  float len = 0.0f;
+  source_coords(g, src, r, j, c, &len);
+  T *row = E + q * ld;
+  for (int k = 0; k < 4; ++k) row[k] = to_t<T>((float)c[k]);
+  float sc[2 * kMaxFreq];
+  for (int k = 0; k < 4; ++k) {
+    octave_features(c[k], F, sc);
+    for (int l = 0; l < 2 * F; ++l) row[4 + 2 * F * k + l] = to_t<T>(sc[l]);
+  }
+  for (int k = 4 + 8 * F; k < ld; ++k) row[k] = to_t<T>(0.0f);
+  if (j == 0) {
+    if (ray_l) ray_l[r] = len;
+    if (ray_p) ray_p[r] = proj ? proj[src.idx[r]] : 0.0f;
+  }
+}
+
+void launch_encode_f32(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
+                       int F, int ld, float *E, float *ray_l, const float *proj,
+                       float *ray_p, cudaStream_t st) {
+  long long n = n_rays * S;
+  k_encode<float><<<ceil_div(n, 128), 128, 0, st>>>(g, src, n_rays, S, F, ld, E, ray_l, proj,
+                                                     ray_p);
+}
+void launch_encode_bf16(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
+                        int F, int ld, __nv_bfloat16 *E, float *ray_l, const float *proj,
+                        float *ray_p, cudaStream_t st) {
+  long long n = n_rays * S;
+  k_encode<__nv_bfloat16><<<ceil_div(n, 128), 128, 0, st>>>(g, src, n_rays, S, F, ld, E, ray_l,
+                                                             proj, ray_p);
+}
+
+// ------------------------------------- output layer, forward model, loss
+// One warp per ray; lanes split the W columns of each sample's dot product.
+__global__ void k_out_segsum_f32(const float *zH, long long ld, int W, int act, int out_act,
+                                 const float *w_out, const float *b_out, long long n_rays,
+                                 int S, float mu0, const float *ray_l, const float *ray_p,
+                                 float inv_B, int train, float *z_out, float *p_bar,
+                                 float *sq, float *dz) {
+  long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (r >= n_rays) return;
+  float bo = b_out[0];
+  float sumM = 0.0f;
+  for (int j = 0; j < S; ++j) {
+    const float *row = zH + (r * S + j) * ld;
+    float acc = 0.0f;
+    for (int c = lane; c < W; c += 32) acc += act_f(row[c], act) * w_out[c];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    float z = acc + bo;
+    if (lane == 0) z_out[r * S + j] = z;
+    sumM += out_f(z, out_act);
+  }
+  float l = ray_l[r];
+  float pb = mu0 * (l / S) * sumM;
+  if (lane == 0) {
+    p_bar[r] = pb;
+    if (train) {
+      float res = pb - ray_p[r];
+      sq[r] = res * res;
+    }
+  }
+  if (!train) return;
+  __syncwarp();
+  float coef = 2.0f * inv_B * (pb - ray_p[r]) * mu0 * (l / S);
+  for (int j = lane; j < S; j += 32) dz[r * S + j] = coef * out_grad_f(z_out[r * S + j], out_act);
+}
+
+void launch_out_segsum_f32(const float *zH, long long ld, int W, int act, int out_act,
+                           const float *w_out, const float *b_out, long long n_rays, int S,
+                           float mu0, const float *ray_l, const float *ray_p, float inv_B,
+                           bool train, float *z_out, float *p_bar, float *sq, float *dz,
+                           cudaStream_t st) {
+  k_out_segsum_f32<<<ceil_div(n_rays * 32, 256), 256, 0, st>>>(
+      zH, ld, W, act, out_act, w_out, b_out, n_rays, S, mu0, ray_l, ray_p, inv_B, train ? 1 : 0,
+      z_out, p_bar, sq, dz);
+}
+
+// Warp-segmented forward model from per-sample outputs: each warp reduces
+// one ray's S outputs in a fixed order (lane-strided partial sums, then a
+// butterfly), then forms the residual and the per-sample adjoint.
+__global__ void k_segsum(const float *z_out, int out_act, long long n_rays, int S, float mu0,
+                         const float *ray_l, const float *ray_p, float inv_B, int train,
+                         float *p_bar, float *sq, float *dz) {
+  long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (r >= n_rays) return;
+  const float *z = z_out + r * S;
+  float s = 0.0f;
+  for (int j = lane; j < S; j += 32) s += out_f(z[j], out_act);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  float l = ray_l[r];
+  float pb = mu0 * (l / S) * s;
+  if (lane == 0) {
+    p_bar[r] = pb;
+    if (train) {
+      float res = pb - ray_p[r];
+      sq[r] = res * res;
+    }
+  }
+  if (!train) return;
+  float coef = 2.0f * inv_B * (pb - ray_p[r]) * mu0 * (l / S);
+  for (int j = lane; j < S; j += 32) dz[r * S + j] = coef * out_grad_f(z[j], out_act);
+}
+
+void launch_segsum(const float *z_out, int out_act, long long n_rays, int S, float mu0,
+                   const float *ray_l, const float *ray_p, float inv_B, bool train,
+                   float *p_bar, float *sq, float *dz, cudaStream_t st) {
+  k_segsum<<<ceil_div(n_rays * 32, 256), 256, 0, st>>>(z_out, out_act, n_rays, S, mu0, ray_l,
+                                                       ray_p, inv_B, train ? 1 : 0, p_bar, sq,
+                                                       dz);
+}
+
+__global__ void k_out_delta_f32(const float *dz, const float *w_out, const float *zH,
+                                long long ld, int W, int act, long long n, float *D) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n * W) return;
+  long long s = q / W;
+  int c = (int)(q - s * W);
+  D[s * W + c] = dz[s] * w_out[c] * act_grad_f(zH[s * ld + c], act);
+}
+void launch_out_delta_f32(const float *dz, const float *w_out, const float *zH, long long ld,
+                          int W, int act, long long n, float *D, cudaStream_t st) {
+  k_out_delta_f32<<<ceil_div(n * W, 256), 256, 0, st>>>(dz, w_out, zH, ld, W, act, n, D);
+}
+
+// ------------------------------------------------------ column sums
+int colsum_splits(long long rows) {
+  long long s = (rows + 2047) / 2048;
+  return (int)(s < 1 ? 1 : (s > 1184 ? 1184 : s));
+}
+
+__global__ void k_colsum(const float *X, long long ld, int C, long long rows, const float *w,
+                         int apply_act, int act, int splits, float *part) {
+  int z = blockIdx.y;
+  long long per = (rows + splits - 1) / splits;
+  long long r0 = z * per, r1 = r0 + per < rows ? r0 + per : rows;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+    for (long long r = r0; r < r1; ++r) {
+      float x = X[r * ld + c];
+      if (apply_act) x = act_f(x, act);
+      acc += w ? w[r] * x : x;
+    }
+    part[(long long)z * C + c] = acc;
+  }
+}
+void launch_colsum(const float *X, long long ld, int C, long long rows, const float *w,
+                   bool apply_act, int act, int splits, float *part, cudaStream_t st) {
+  dim3 grid(ceil_div(C, 256), splits);
+  k_colsum<<<grid, 256, 0, st>>>(X, ld, C, rows, w, apply_act ? 1 : 0, act, splits, part);
+}
+
+__global__ void k_reduce_partials(const float *part, int splits, long long C, float *out,
+                                  int accumulate) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  float acc = accumulate ? out[c] : 0.0f;
+  float s = 0.0f;
+  for (int z = 0; z < splits; ++z) s += part[(long long)z * C + c];
+  out[c] = acc + s;
+}
+void launch_reduce_partials(const float *part, int splits, long long C, float *out,
+                            bool accumulate, cudaStream_t st) {
+  k_reduce_partials<<<ceil_div(C, 256), 256, 0, st>>>(part, splits, C, out, accumulate ? 1 : 0);
+}
+
+// One block, fixed order: strided partial sums then a tree.
+__global__ void k_loss_sum(const float *sq, long long n, float inv_B, float *loss,
+                           int accumulate) {
+  __shared__ float red[1024];
+  float s = 0.0f;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += sq[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[0] = (accumulate ? loss[0] : 0.0f) + inv_B * red[0];
+}
+void launch_loss_sum(const float *sq, long long n, float inv_B, float *loss, bool accumulate,
+                     cudaStream_t st) {
+  k_loss_sum<<<1, 1024, 0, st>>>(sq, n, inv_B, loss, accumulate ? 1 : 0);
+}
+
+// ------------------------------------------------------------------- Adam
+__global__ void k_adam(float *theta, float *m, float *v, const float *g, long long P, float lr,
+                       float beta1, float beta2, float eps, float bc1, float bc2) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  float gi = g[i];
+  float mi = beta1 * m[i] + (1.0f - beta1) * gi;
+  float vi = beta2 * v[i] + (1.0f - beta2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi * bc1) / (sqrtf(vi * bc2) + eps);
+}
+void launch_adam(float *theta, float *m, float *v, const float *g, long long P, float lr,
+                 float beta1, float beta2, float eps, float bc1, float bc2, cudaStream_t st) {
+  k_adam<<<ceil_div(P, 256), 256, 0, st>>>(theta, m, v, g, P, lr, beta1, beta2, eps, bc1, bc2);
+}
+
+}  // namespace dinr
