@@ -1,0 +1,322 @@
+"""Benchmark of one stochastic DINR training step on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--prec bf16|fp32] [--no-cpu-baseline]
+
+Workload: parallel beam, 512 views over 4 rotations, 128 x 128 detector,
+128 samples per ray, 10-octave encoding (84 inputs), MLP 5 x 256 ReLU,
+65,536 rays per step (8,388,608 samples); 16 moving, growing ellipsoids
+give the measurements. A step is the whole hot path: minibatch draw, ray
+generation, encoding, MLP forward, forward model and loss, backward, Adam.
+Metric: training ray-samples per second (whole job over all ranks).
+
+Our arm runs the library (default BF16 tensor-core path; the plain FP32 path
+is timed beside it). The reference arm (--impl reference) times the FP64 CPU
+oracle on a bounded ray sample of the same workload on the host cores.
+One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "train ray-samples/s"
+WORKLOAD = 2
+FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def config(w, extra=None):
+    g, net = w.geom, w.net
+    c = {"workload": "parallel-beam 512 views x 128x128 detector, S=128, 10-octave encoding, "
+                     "MLP 5x256 ReLU, 65536 rays/step",
+         "rays_per_step": w.train.batch_rays, "samples_per_ray": g.samples_per_ray,
+         "samples_per_step": w.train.batch_rays * g.samples_per_ray,
+         "mlp": f"{net.hidden_layers}x{net.width}", "d_in": net.d_in,
+         "l2": "inputs larger than L2 (activations of a step are tens of GB)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def algorithmic_flops_per_sample(net):
+    """2 * sum(fan_in * fan_out) forward, twice that backward minus the
+    first layer's input gradient (not computed)."""
+    pw = sum(o * i for o, i in net.layer_shapes())
+    return 2 * pw + 4 * pw - 2 * net.d_in * net.width
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        for ln in out.splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) >= 8:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        load = [r for r in self.rows if (num(r[3]) or 0) > 50] or self.rows
+        sm = [num(r[0]) for r in load if num(r[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in load for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(load[0][1]), "samples": len(load), "reasons": reasons}
+
+
+def oracle_rate(w, n_rays, seed=11):
+    """The FP64 oracle's samples/s on n_rays rays of the workload (one full
+    forward + backward + Adam step on that sample)."""
+    from oracle import phantom as oph, step as ostep
+    from synthetic import workloads as wl
+    g, net = w.geom, w.net
+    idx = wl.ray_subset(g.n_proj, n_rays, seed)
+    proj = np.zeros(g.n_proj)
+    proj[idx] = oph.projections(wl.phantom(w), g, idx)
+    th = wl.he_init(net, w.seeds["weights"])
+    t0 = time.perf_counter()
+    ostep.train_step(th, np.zeros_like(th), np.zeros_like(th), 1, g, net, w.train, idx, proj)
+    dt = time.perf_counter() - t0
+    return n_rays * g.samples_per_ray / dt, dt
+
+
+def cpu_baseline(w, n_rays=2048):
+    rate, dt = oracle_rate(w, n_rays)
+    return {"value": rate, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_rays} rays x {w.geom.samples_per_ray} samples of the workload, one "
+                      f"FP64 step (numpy, BLAS threads = host cores), {dt:.1f} s"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    from synthetic import workloads as wl
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = wl.workload(WORKLOAD)
+    n_rays = 256
+    for _ in range(args.warmup):
+        oracle_rate(w, n_rays, seed=7)
+    rates, total = [], 0.0
+    for k in range(args.steps):
+        r, dt = oracle_rate(w, n_rays, seed=100 + k)
+        rates.append(r)
+        total += dt
+    value = args.steps * n_rays * w.geom.samples_per_ray / total
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": config(w, {"reference_sample_rays_per_step": n_rays}),
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{n_rays} rays x {w.geom.samples_per_ray} samples per step"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_steps(model, steps, n):
+    import torch
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(steps):
+        model.train_step(None, n=n, sync=False)
+    b.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_19075_b300 import Dinr, DinrError, phantom_project
+    from synthetic import workloads as wl
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    w = wl.workload(WORKLOAD)
+    g, net = w.geom, w.net
+    B, S = w.train.batch_rays, g.samples_per_ray
+    proj = phantom_project(g, wl.phantom(w))            # measurements, resident in HBM
+    theta = wl.he_init(net, w.seeds["weights"]).astype(np.float32)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    results = {}
+    precs = [args.prec] + ([p for p in ("fp32",) if p != args.prec] if args.compare else [])
+    for prec in precs:
+        try:
+            m = Dinr(g, net, w.train, proj, prec=prec, init_params=theta,
+                     sampler_seed=w.seeds["sampler"] + 1000 * rank)
+        except DinrError as e:
+            results[prec] = {"error": str(e)}
+            continue
+        steps = args.steps if prec == args.prec else max(2, args.steps // 4)
+        for _ in range(args.warmup):
+            m.train_step(None, n=B, sync=False)
+        barrier()
+        m.profile(True)
+        with Clocks(local) as ck:
+            barrier()
+            dt = time_steps(m, steps, B)
+            barrier()
+        m.profile(False)
+        prof = m.profile_report()
+        if ws > 1:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = t.item()
+        loss = m.loss()
+        # end to end through the public API: host indices (pinned) in, loss out
+        idx_host = torch.empty(B, dtype=torch.int64).pin_memory()
+        rng = np.random.default_rng(rank)
+        e2e_steps = max(2, steps // 2)
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            idx_host.numpy()[:] = rng.integers(0, g.n_proj, B)
+            m.train_step(idx_host.numpy(), sync=True)
+        barrier()
+        e2e_dt = time.perf_counter() - t0
+        results[prec] = dict(dt=dt, steps=steps, prof=prof, clocks=ck.summary(), loss=loss,
+                             e2e=ws * e2e_steps * B * S / e2e_dt)
+        m.close()
+    if rank == 0:
+        emit(args, w, results, ws)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def emit(args, w, results, ws):
+    g, net = w.geom, w.net
+    B, S = w.train.batch_rays, g.samples_per_ray
+    main = results[args.prec]
+    if "error" in main:
+        print(json.dumps({"metric": METRIC, "error": main["error"]}), flush=True)
+        return
+    pk, src = peaks()
+    value = ws * main["steps"] * B * S / main["dt"]
+    prof = main["prof"]
+    launches = prof.pop("total_launches", {}).get("launches")
+    kern = {k: v for k, v in prof.items()}
+    top = max(kern, key=lambda k: kern[k]["ms"])
+    tk = kern[top]
+    if args.prec == "bf16":
+        achieved = tk["flops"] / (tk["ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "peak_source": f"bf16_tflops_sustained ({src})"}
+    else:
+        achieved = tk["flops"] / (tk["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = top
+    roof["launches"] = tk["launches"]
+    roof["traffic"] = None
+    total_ms = sum(v["ms"] for v in kern.values())
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,
+            "steps": main["steps"], "warmup": args.warmup,
+            "ms_per_step": 1e3 * main["dt"] / main["steps"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": config(w, {"parallelism": f"replicas{ws}" if ws > 1 else "single GPU",
+                                 "prec": args.prec}),
+            "tflops_algorithmic": value * algorithmic_flops_per_sample(net) / 1e12,
+            "roofline": roof,
+            "kernel_shares": {k: round(v["ms"] / total_ms, 4) for k, v in kern.items()},
+            "clocks": main["clocks"], "gpu_launches": launches,
+            "e2e": {"value": main["e2e"], "unit": "samples/s", "h2d_bytes_per_step": 8 * B,
+                    "d2h_bytes_per_step": 4},
+            "loss_last": main["loss"]}
+    for p, r in results.items():
+        if p != args.prec:
+            line[f"{p}_path"] = ({"error": r["error"]} if "error" in r else
+                                 {"value": ws * r["steps"] * B * S / r["dt"], "unit": "samples/s",
+                                  "ms_per_step": 1e3 * r["dt"] / r["steps"]})
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-compare", dest="compare", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -228,6 +228,18 @@ DINR_API dinr_status dinr_phantom_project(const dinr_geometry *geom, int n_ell,
                                  double growth, const int64_t *idx_dev,
                                  int64_t n, float *out_dev, void *cuda_stream);
 
+/* Per-kernel timing of the context's own launches with CUDA events on its
+ * stream (tracing; no counterpart in the paper). dinr_profile(ctx, 1)
+ * clears and starts recording, 0 stops. dinr_profile_report waits for the
+ * stream and writes one line per kernel class,
+ *   "<name> <launches> <total_ms> <flops> <bytes>\n"
+ * (flops and bytes: algorithmic totals over the recorded launches), then
+ * "total_launches <n> 0 0 0" counting every kernel the context launched
+ * since profiling started, into buf of size `size` (truncated,
+ * NUL-terminated). */
+DINR_API dinr_status dinr_profile(dinr_ctx *ctx, int enable);
+DINR_API dinr_status dinr_profile_report(dinr_ctx *ctx, char *buf, size_t size);
+
 /* Wait for all work of the context. */
 DINR_API dinr_status dinr_synchronize(dinr_ctx *ctx);
 

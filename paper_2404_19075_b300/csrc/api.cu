@@ -35,7 +35,11 @@ int dinr_fail(dinr_ctx *c, int status, const char *fmt, ...) {
       return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "%s: %s (%s:%d)", #call,        \
                                     cudaGetErrorString(e_), __FILE__, __LINE__);      \
   } while (0)
-#define CKL() CK(cudaGetLastError())
+#define CKL()            \
+  do {                   \
+    ++c->launches;       \
+    CK(cudaGetLastError()); \
+  } while (0)
 #define LIVE(c)                                                                       \
   do {                                                                                \
     if (!(c)) return DINR_ERR_ARG;                                                    \
@@ -282,6 +286,7 @@ void dinr_destroy(dinr_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
   destroy_backend(c);
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -365,9 +370,12 @@ dinr_status dinr_train_step(dinr_ctx *c, const int64_t *idx, int n, int on_devic
   double lr = c->lr * std::pow(c->decay, (double)(c->step / spe));
   double bc1 = 1.0 / (1.0 - std::pow(c->b1, (double)t));
   double bc2 = 1.0 / (1.0 - std::pow(c->b2, (double)t));
-  launch_adam(c->d_params, c->d_m, c->d_v, c->d_grad, c->P, (float)lr, (float)c->b1,
-              (float)c->b2, (float)c->eps, (float)bc1, (float)bc2, c->st);
-  CKL();
+  {
+    ProfScope ps(c, "adam", 0.0, 28.0 * c->P);
+    launch_adam(c->d_params, c->d_m, c->d_v, c->d_grad, c->P, (float)lr, (float)c->b1,
+                (float)c->b2, (float)c->eps, (float)bc1, (float)bc2, c->st);
+    CKL();
+  }
   s = after_param_update(c);
   if (s != DINR_OK) return s;
   c->step = t;
@@ -582,4 +590,75 @@ dinr_status dinr_phantom_project(const dinr_geometry *geom, int n_ell, const dou
   if (s != DINR_OK) dinr_fail(nullptr, s, "phantom projection failed (%s)", tmp.err);
   for (void *p : tmp.allocs) cudaFree(p);
   return s;
+}
+
+// ------------------------------------------------------------ profiling
+static cudaEvent_t prof_event(dinr_ctx *c) {
+  if (c->prof_used == c->prof_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->prof_pool.push_back(e);
+  }
+  return c->prof_pool[c->prof_used++];
+}
+
+ProfScope::ProfScope(dinr_ctx *ctx, const char *name, double flops, double bytes) : c(ctx) {
+  if (!c || !c->prof) return;
+  int cls = -1;
+  for (size_t i = 0; i < c->prof_names.size(); ++i)
+    if (c->prof_names[i] == name) cls = (int)i;
+  if (cls < 0) {
+    c->prof_names.push_back(name);
+    cls = (int)c->prof_names.size() - 1;
+  }
+  ProfRec r{cls, prof_event(c), prof_event(c), flops, bytes};
+  if (!r.a || !r.b) return;
+  cudaEventRecord(r.a, c->st);
+  c->prof_recs.push_back(r);
+  idx = (int)c->prof_recs.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx >= 0) cudaEventRecord(c->prof_recs[idx].b, c->st);
+}
+
+dinr_status dinr_profile(dinr_ctx *c, int enable) {
+  LIVE(c);
+  CK(cudaStreamSynchronize(c->st));
+  c->prof = enable != 0;
+  if (enable) {
+    c->prof_recs.clear();
+    c->prof_names.clear();
+    c->prof_used = 0;
+    c->launches = 0;
+  }
+  return DINR_OK;
+}
+
+dinr_status dinr_profile_report(dinr_ctx *c, char *buf, size_t size) {
+  LIVE(c);
+  if (!buf || size == 0) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "no buffer");
+  CK(cudaStreamSynchronize(c->st));
+  size_t n = c->prof_names.size();
+  std::vector<double> ms(n, 0.0), fl(n, 0.0), by(n, 0.0);
+  std::vector<long long> cnt(n, 0);
+  for (const ProfRec &r : c->prof_recs) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.cls] += t;
+    fl[r.cls] += r.flops;
+    by[r.cls] += r.bytes;
+    cnt[r.cls] += 1;
+  }
+  std::string out;
+  char line[256];
+  for (size_t i = 0; i < n; ++i) {
+    snprintf(line, sizeof(line), "%s %lld %.6f %.6e %.6e\n", c->prof_names[i].c_str(), cnt[i],
+             ms[i], fl[i], by[i]);
+    out += line;
+  }
+  snprintf(line, sizeof(line), "total_launches %lld 0 0 0\n", c->launches);
+  out += line;
+  snprintf(buf, size, "%s", out.c_str());
+  return DINR_OK;
 }

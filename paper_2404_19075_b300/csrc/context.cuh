@@ -5,7 +5,15 @@
 #include "../../include/dinr.h"
 #include "internal.cuh"
 
+#include <string>
 #include <vector>
+
+// One recorded launch (or group of launches) of the context.
+struct ProfRec {
+  int cls;                 // index into dinr_ctx::prof_names
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
 
 struct dinr_ctx {
   cudaStream_t st = nullptr;
@@ -43,12 +51,29 @@ struct dinr_ctx {
   // BF16 (tensor-core) backend state, owned by the tensor-core pipeline.
   void *tc = nullptr;
 
+  // per-kernel event timing (dinr_profile)
+  bool prof = false;
+  std::vector<std::string> prof_names;
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  size_t prof_used = 0;
+  long long launches = 0;  // kernels launched by this context
+
   char err[512] = "no error";
   bool failed = false;
   std::vector<void *> allocs;
 };
 
 int dinr_fail(dinr_ctx *c, int status, const char *fmt, ...);
+
+// Brackets the launches issued in its scope with two events on the context
+// stream when profiling is on.
+struct ProfScope {
+  dinr_ctx *c;
+  int idx = -1;
+  ProfScope(dinr_ctx *ctx, const char *name, double flops, double bytes);
+  ~ProfScope();
+};
 
 // Pipeline (pipeline.cu)
 bool bf16_supported(const dinr_net *net);

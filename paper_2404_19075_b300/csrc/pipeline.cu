@@ -17,7 +17,11 @@ using namespace dinr;
       return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "%s: %s (%s:%d)", #call,        \
                                     cudaGetErrorString(e_), __FILE__, __LINE__);      \
   } while (0)
-#define CKL() CK(cudaGetLastError())
+#define CKL()            \
+  do {                   \
+    ++c->launches;       \
+    CK(cudaGetLastError()); \
+  } while (0)
 
 static constexpr long long kMaxPartialFloats = 64LL << 20;
 
@@ -91,6 +95,7 @@ static dinr_status f32_hidden(dinr_ctx *c, long long ns) {
     a.ldc = c->W;
     a.bias = c->d_params + c->offb[L];
     a.k_per_split = a.K;
+    ProfScope ps(c, "sgemm_fwd", 2.0 * ns * c->W * a.K, 4.0 * ns * (a.K + c->W));
     if (launch_sgemm(a, true, true, L > 0, false, kEpiBias, 1, c->st) != 0)
       return (dinr_status)dinr_fail(c, DINR_ERR_UNSUPPORTED, "sgemm variant");
     CKL();
@@ -143,12 +148,17 @@ static dinr_status f32_backward(dinr_ctx *c, long long ns, bool acc) {
     a.C = c->part;
     a.ldc = K_in;
     int splits = dw_splits(ns, c->W, K_in);
+    long long cap = c->part_floats / ((long long)c->W * K_in);
+    if (splits > cap) splits = (int)(cap < 1 ? 1 : cap);
     a.k_per_split = ((ns + splits - 1) / splits + 7) / 8 * 8;
     splits = (int)((ns + a.k_per_split - 1) / a.k_per_split);
     a.split_stride = (long long)c->W * K_in;
-    if (launch_sgemm(a, false, false, false, L > 0, kEpiPartial, splits, c->st) != 0)
-      return (dinr_status)dinr_fail(c, DINR_ERR_UNSUPPORTED, "sgemm variant");
-    CKL();
+    {
+      ProfScope ps(c, "sgemm_dw", 2.0 * ns * c->W * K_in, 4.0 * ns * (c->W + K_in));
+      if (launch_sgemm(a, false, false, false, L > 0, kEpiPartial, splits, c->st) != 0)
+        return (dinr_status)dinr_fail(c, DINR_ERR_UNSUPPORTED, "sgemm variant");
+      CKL();
+    }
     launch_reduce_partials(c->part, splits, (long long)c->W * K_in, c->d_grad + c->offW[L], acc,
                            c->st);
     CKL();
@@ -169,6 +179,7 @@ static dinr_status f32_backward(dinr_ctx *c, long long ns, bool acc) {
       b.Zp = c->Z + (long long)(L - 1) * ns * c->W;
       b.ldz = c->W;
       b.k_per_split = b.K;
+      ProfScope ps(c, "sgemm_dx", 2.0 * ns * c->W * c->W, 4.0 * ns * 3 * c->W);
       if (launch_sgemm(b, true, false, false, false, kEpiMask, 1, c->st) != 0)
         return (dinr_status)dinr_fail(c, DINR_ERR_UNSUPPORTED, "sgemm variant");
       CKL();
@@ -188,9 +199,12 @@ static dinr_status f32_loss_grad(dinr_ctx *c, int n) {
     SourceArgs src{};
     src.kind = kSrcTrainRays;
     src.idx = c->d_idx + r0;
-    launch_encode_f32(c->geo, src, nr, c->S, c->F, c->ldE, c->E, c->ray_l, c->d_proj, c->ray_p,
-                      c->st);
-    CKL();
+    {
+      ProfScope ps(c, "encode", 0.0, 4.0 * ns * c->ldE);
+      launch_encode_f32(c->geo, src, nr, c->S, c->F, c->ldE, c->E, c->ray_l, c->d_proj,
+                        c->ray_p, c->st);
+      CKL();
+    }
     dinr_status s = f32_hidden(c, ns);
     if (s != DINR_OK) return s;
     launch_out_segsum_f32(zlast(c, ns), c->W, c->W, c->act, c->out_act,

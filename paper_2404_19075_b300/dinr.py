@@ -198,6 +198,19 @@ class Dinr:
         buf = C.create_string_buffer(blob, len(blob))
         self._c(_abi.lib().dinr_set_state(self._h, buf, len(blob)))
 
+    def profile(self, enable: bool):
+        self._c(_abi.lib().dinr_profile(self._h, 1 if enable else 0))
+
+    def profile_report(self) -> dict:
+        """{kernel: dict(launches, ms, flops, bytes)} of the recorded launches."""
+        buf = C.create_string_buffer(1 << 16)
+        self._c(_abi.lib().dinr_profile_report(self._h, buf, len(buf)))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, n, ms, fl, by = line.split()
+            out[name] = dict(launches=int(n), ms=float(ms), flops=float(fl), bytes=float(by))
+        return out
+
     def synchronize(self):
         self._c(_abi.lib().dinr_synchronize(self._h))
 
