@@ -238,7 +238,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for k in range(e2e_steps):
             idx_host.numpy()[:] = rng.integers(0, g.n_proj, B)
-            m.train_step(idx_host.numpy(), sync=True)
+            m.train_step_host(idx_host, sync=True)
         barrier()
         e2e_dt = time.perf_counter() - t0
         results[prec] = dict(dt=dt, steps=steps, prof=prof, clocks=ck.summary(), loss=loss,

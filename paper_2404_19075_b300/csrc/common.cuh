@@ -93,10 +93,10 @@ __device__ __forceinline__ Ray make_ray(const GeoDev &g, long long i) {
   return ray_at(g, u, v, cs.x, cs.y, g.view_tbar[m]);
 }
 
-// Normalised sample j of a ray (App. A midpoints; App. B item 1), FP64.
-__device__ __forceinline__ void sample_coords(const GeoDev &g, const Ray &r, int j,
+// Normalised sample j of S on a ray (App. A midpoints; App. B item 1), FP64.
+__device__ __forceinline__ void sample_coords(const GeoDev &g, const Ray &r, int j, int S,
                                               double &zb, double &yb, double &xb) {
-  double s = r.s0 + (j + 0.5) * (r.l / g.S);
+  double s = r.s0 + (j + 0.5) * (r.l / S);
   double x = r.ox + s * r.dx, y = r.oy + s * r.dy, z = r.oz + s * r.dz;
   xb = x * g.inv_R;
   yb = y * g.inv_R;

@@ -109,11 +109,12 @@ __device__ __forceinline__ Ray source_ray(const GeoDev &g, const SourceArgs &s, 
 
 // Normalised (t, z, y, x) of sample j of ray/point slot r.
 __device__ __forceinline__ void source_coords(const GeoDev &g, const SourceArgs &s,
-                                              long long r, int j, double c[4], float *len) {
+                                              long long r, int j, int S, double c[4],
+                                              float *len) {
   if (s.kind == kSrcTrainRays || s.kind == kSrcVirtualView) {
     Ray ray = source_ray(g, s, r);
     c[0] = ray.tbar;
-    sample_coords(g, ray, j, c[1], c[2], c[3]);
+    sample_coords(g, ray, j, S, c[1], c[2], c[3]);
     *len = (float)ray.l;
   } else if (s.kind == kSrcPoints) {
     const float *p = s.points + 4 * (s.first + r);
@@ -158,7 +159,7 @@ __global__ void k_encode(GeoDev g, SourceArgs src, long long n_rays, int S, int 
   int j = (int)(q - r * S);
   double c[4];
   float len = 0.0f;
-  source_coords(g, src, r, j, c, &len);
+  source_coords(g, src, r, j, S, c, &len);
   T *row = E + q * ld;
   for (int k = 0; k < 4; ++k) row[k] = to_t<T>((float)c[k]);
   float sc[2 * kMaxFreq];

@@ -119,12 +119,27 @@ class Dinr:
         return t, t.numel(), 1
 
     def train_step(self, idx=None, n=None, sync=True):
-        """One step; returns the loss (float) when sync, else None."""
+        """One step; returns the loss (float) when sync, else None.
+        idx: None (built-in sampler, n rays), a CUDA tensor or an array
+        (moved to the device first)."""
         t, m, on_dev = self._idx(idx)
         n = m if t is not None else (n or 0)
         out = C.c_float()
         self._c(_abi.lib().dinr_train_step(self._h, _ptr(t), n, on_dev,
                                            C.byref(out) if sync else None))
+        return out.value if sync else None
+
+    def train_step_host(self, idx_host, sync=True):
+        """One step with indices in host memory (an int64 numpy array or a
+        CPU tensor, ideally pinned); the library copies them itself."""
+        if isinstance(idx_host, torch.Tensor):
+            assert idx_host.device.type == "cpu" and idx_host.dtype == torch.int64
+            ptr, n = C.c_void_p(idx_host.data_ptr()), idx_host.numel()
+        else:
+            a = np.ascontiguousarray(idx_host, np.int64)
+            ptr, n = C.c_void_p(a.ctypes.data), a.size
+        out = C.c_float()
+        self._c(_abi.lib().dinr_train_step(self._h, ptr, n, 0, C.byref(out) if sync else None))
         return out.value if sync else None
 
     def loss_grad(self, idx=None, n=None):

@@ -136,15 +136,29 @@ def test_c1_autograd_function(c1):
 def test_bad_indices_are_rejected(c1):
     from paper_2404_19075_b300 import DinrError
     w, m, theta, proj, idx, ref = c1
-    with pytest.raises(DinrError):
-        m.train_step(np.array([0, w.geom.n_proj], np.int64))       # host: checked up front
-    bad = torch.tensor([1, -5, 3], dtype=torch.int64, device="cuda")
     st = m.get_state()
     with pytest.raises(DinrError):
-        m.train_step(bad)                                             # device: sanitised, reported
-    m.set_state(st)
+        m.train_step_host(np.array([0, w.geom.n_proj], np.int64))   # host: checked up front
+    assert m.get_state() == st                                       # nothing ran
+    bad = torch.tensor([1, -5, 3], dtype=torch.int64, device="cuda")
+    with pytest.raises(DinrError):
+        m.train_step(bad)                             # device: replaced by 0, then reported
     with pytest.raises(DinrError):
         m.train_step(None, n=0)
+    with pytest.raises(DinrError):
+        m.train_step(None, n=1025)                    # more than the batch the context holds
+    m.set_state(st)
+
+
+def test_host_and_device_indices_agree(c1):
+    w, m, theta, proj, idx, ref = c1
+    st = m.get_state()
+    l_host = m.train_step_host(idx)
+    p_host = m.params().cpu().numpy()
+    m.set_state(st)
+    l_dev = m.train_step(torch.as_tensor(idx, device="cuda"))
+    assert l_host == l_dev and np.array_equal(p_host, m.params().cpu().numpy())
+    m.set_state(st)
 
 
 # ------------------------------------------------------- queries (Sec. V)
@@ -155,6 +169,7 @@ def test_c1_query_project_grid(c1):
     rng = np.random.default_rng(3)
     coords = np.stack([rng.uniform(0, 1, 500), rng.uniform(-1, 1, 500),
                        rng.uniform(-0.7, 0.7, 500), rng.uniform(-0.7, 0.7, 500)], 1)
+    coords = coords.astype(np.float32).astype(np.float64)       # what the device sees
     assert_close(m.query(coords).cpu().numpy(), ostep.query(theta, g, net, coords), TOL, "query")
     img = m.project(0.3, 0.41, 17, 23, 19).cpu().numpy()
     want = ostep.project_view(theta, g, net, 0.3, 0.41, 17, 23, 19)
