@@ -295,8 +295,7 @@ const char *dinr_last_error(const dinr_ctx *c) { return c ? c->err : g_create_er
 
 dinr_status dinr_synchronize(dinr_ctx *c) {
   LIVE(c);
-  CK(cudaStreamSynchronize(c->st));
-  return DINR_OK;
+  return backend_poll(c);
 }
 
 dinr_status dinr_set_projections(dinr_ctx *c, const float *proj, int on_device) {
@@ -385,7 +384,8 @@ dinr_status dinr_train_step(dinr_ctx *c, const int64_t *idx, int n, int on_devic
   }
   if (loss_out) {
     CK(cudaMemcpyAsync(loss_out, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
+    s = backend_poll(c);
+    if (s != DINR_OK) return s;
     if (!std::isfinite(*loss_out))
       return (dinr_status)dinr_fail(c, DINR_ERR_NONFINITE, "loss is not finite");
   }
@@ -471,16 +471,14 @@ dinr_status dinr_get_grads(dinr_ctx *c, float *host) {
   LIVE(c);
   if (!host) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "host is NULL");
   CK(cudaMemcpyAsync(host, c->d_grad, sizeof(float) * c->P, cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
-  return DINR_OK;
+  return backend_poll(c);
 }
 
 dinr_status dinr_get_loss(dinr_ctx *c, float *host) {
   LIVE(c);
   if (!host) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "host is NULL");
   CK(cudaMemcpyAsync(host, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
-  return DINR_OK;
+  return backend_poll(c);
 }
 
 // ------------------------------------------------------------ state blob

@@ -87,5 +87,7 @@ dinr_status run_forward_rays(dinr_ctx *c, const dinr::SourceArgs &src, long long
                              float *out);
 // mu0 * M at n points of a source into out.
 dinr_status run_forward_points(dinr_ctx *c, const dinr::SourceArgs &src, long long n, float *out);
+// Waits for the stream; reports device-side failures recorded by kernels.
+dinr_status backend_poll(dinr_ctx *c);
 // Refresh derived copies of the parameters (BF16 weights) after a change.
 dinr_status after_param_update(dinr_ctx *c);

@@ -297,13 +297,17 @@ __global__ void k_colsum(const float *X, long long ld, int C, long long rows, co
   long long per = (rows + splits - 1) / splits;
   long long r0 = z * per, r1 = r0 + per < rows ? r0 + per : rows;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-    float acc = 0.0f;
+    float acc = 0.0f, blk = 0.0f;     // blocked summation, blocks of 256 rows
     for (long long r = r0; r < r1; ++r) {
       float x = X[r * ld + c];
       if (apply_act) x = act_f(x, act);
-      acc += w ? w[r] * x : x;
+      blk += w ? w[r] * x : x;
+      if (((r - r0) & 255) == 255) {
+        acc += blk;
+        blk = 0.0f;
+      }
     }
-    part[(long long)z * C + c] = acc;
+    part[(long long)z * C + c] = acc + blk;
   }
 }
 void launch_colsum(const float *X, long long ld, int C, long long rows, const float *w,

@@ -67,6 +67,18 @@ __global__ void __launch_bounds__(256) k_sgemm(SgemmArgs a) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
 
+  // Weight-gradient sums run over many thousands of samples: accumulate
+  // blocks of kBlockK samples separately and add each block into the total
+  // (blocked summation keeps the rounding growth near kBlockK + K/kBlockK
+  // instead of K).
+  constexpr bool kBlocked = (EPI == kEpiPartial);
+  constexpr int kBlockK = 256;
+  float tot[kBlocked ? 8 : 1][kBlocked ? 8 : 1];
+#pragma unroll
+  for (int i = 0; i < (kBlocked ? 8 : 1); ++i)
+#pragma unroll
+    for (int j = 0; j < (kBlocked ? 8 : 1); ++j) tot[i][j] = 0.0f;
+
   float ra[4], rb[4];
   load_tile<A_KC>(a.A, a.lda, a.M, kb, ke, m0, A_ACT, a.act, ra);
   load_tile<B_KC>(a.B, a.ldb, a.N, kb, ke, n0, B_ACT, a.act, rb);
@@ -92,6 +104,23 @@ __global__ void __launch_bounds__(256) k_sgemm(SgemmArgs a) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
+    if constexpr (kBlocked) {
+      if (((k0 - kb) / BK + 1) % (kBlockK / BK) == 0 || k0 + BK >= ke) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            tot[i][j] += acc[i][j];
+            acc[i][j] = 0.0f;
+          }
+      }
+    }
+  }
+  if constexpr (kBlocked) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = tot[i][j];
   }
 
   float *C = a.C;

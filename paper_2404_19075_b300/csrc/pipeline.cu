@@ -72,6 +72,12 @@ void destroy_backend(dinr_ctx *c) {
   if (c->prec == DINR_PREC_BF16) tc_destroy(c);
 }
 
+dinr_status backend_poll(dinr_ctx *c) {
+  if (c->prec == DINR_PREC_BF16) return tc_poll(c);
+  CK(cudaStreamSynchronize(c->st));
+  return DINR_OK;
+}
+
 dinr_status after_param_update(dinr_ctx *c) {
   if (c->prec == DINR_PREC_BF16) return tc_params_changed(c);
   return DINR_OK;

@@ -12,3 +12,5 @@ dinr_status tc_loss_grad(dinr_ctx *c, int n);
 dinr_status tc_forward_rays(dinr_ctx *c, const dinr::SourceArgs &src, long long n_rays, int S,
                             float *out);
 dinr_status tc_forward_points(dinr_ctx *c, const dinr::SourceArgs &src, long long n, float *out);
+// Waits for the stream and reports a bounded device wait that gave up.
+dinr_status tc_poll(dinr_ctx *c);

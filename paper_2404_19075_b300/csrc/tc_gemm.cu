@@ -1,0 +1,323 @@
+// Persistent warp-specialised tcgen05 GEMM (see tc_gemm.cuh).
+//
+// Roles per CTA (192 threads, one CTA per SM):
+//   warp 0      one thread issues TMA loads into an S-stage shared ring
+//   warp 1      allocates TMEM; one thread issues tcgen05.mma (K = 16 each)
+//   warps 2..5  epilogue: TMEM -> registers -> fused op -> global memory
+// Accumulators are double-buffered in TMEM when they fit, so the epilogue
+// of one tile overlaps the MMAs of the next. Every mbarrier wait is bounded
+// in time; a timeout sets *err and the roles wind down without hanging.
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+#include <cudaTypedefs.h>
+
+namespace dinr {
+
+using namespace tc;
+
+namespace {
+constexpr int BM = 128, BK = 64;
+constexpr int kThreads = 192;
+constexpr int kOnesBytes = 1024;
+
+struct Smem {
+  uint8_t *a, *b, *ones;
+  uint64_t *full, *empty, *tfull, *tempty, *drain;
+  uint32_t *tslot;
+};
+
+__device__ __forceinline__ Smem carve(uint8_t *base, const TcGemmArgs &p) {
+  Smem s;
+  s.a = base;
+  s.b = base + (size_t)p.stages * p.a_bytes;
+  s.ones = s.b + (size_t)p.stages * p.b_bytes;
+  s.full = reinterpret_cast<uint64_t *>(s.ones + kOnesBytes);
+  s.empty = s.full + p.stages;
+  s.tfull = s.empty + p.stages;
+  s.tempty = s.tfull + 2;
+  s.drain = s.tempty + 2;
+  s.tslot = reinterpret_cast<uint32_t *>(s.drain + 1);
+  return s;
+}
+
+__device__ __forceinline__ int acc_stride(const TcGemmArgs &p) {
+  int cols = p.N + (p.with_db ? 16 : 0);
+  return (cols + 31) / 32 * 32;
+}
+
+__device__ __forceinline__ void tile_range(const TcGemmArgs &p, int t, int &mt, int &sp,
+                                           long long &k0, int &nk) {
+  mt = t % p.m_tiles;
+  sp = t / p.m_tiles;
+  k0 = (long long)sp * p.k_per_split;
+  long long k1 = k0 + p.k_per_split < p.K ? k0 + p.k_per_split : p.K;
+  nk = (int)((k1 - k0 + BK - 1) / BK);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcGemmArgs &p,
+                         const Smem &s) {
+  prefetch_tmap(ta);
+  prefetch_tmap(tb);
+  const int S = p.stages;
+  const uint32_t nb_mn = (uint32_t)((p.N + 63) / 64);
+  const uint32_t tx = (uint32_t)p.a_bytes + (uint32_t)p.b_bytes;
+  uint32_t it = 0;
+  const int n_tiles = p.m_tiles * p.splits;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    int mt, sp, nk;
+    long long k0;
+    tile_range(p, t, mt, sp, k0, nk);
+    for (int kb = 0; kb < nk; ++kb, ++it) {
+      uint32_t st = it % S, rd = it / S;
+      if (!mbar_wait(&s.empty[st], (rd & 1) ^ 1, p.err, 1)) return;
+      mbar_expect_tx(&s.full[st], tx);
+      int kx = (int)(k0 + (long long)kb * BK);
+      uint8_t *da = s.a + (size_t)st * p.a_bytes;
+      uint8_t *db = s.b + (size_t)st * p.b_bytes;
+      if (!p.a_mn) {
+        tma_load_2d(ta, &s.full[st], da, kx, mt * BM);
+      } else {
+        tma_load_2d(ta, &s.full[st], da, mt * BM, kx);
+        tma_load_2d(ta, &s.full[st], da + 8192, mt * BM + 64, kx);
+      }
+      if (!p.b_mn) {
+        tma_load_2d(tb, &s.full[st], db, kx, 0);
+      } else {
+        for (uint32_t j = 0; j < nb_mn; ++j) tma_load_2d(tb, &s.full[st], db + 8192 * j, 64 * j, kx);
+      }
+    }
+  }
+  // Before the CTA can exit, every load issued must have landed.
+  uint32_t n = it < (uint32_t)S ? it : (uint32_t)S;
+  for (uint32_t q = it - n; q < it; ++q) {
+    uint32_t st = q % S, rd = q / S;
+    if (!mbar_wait(&s.full[st], rd & 1, p.err, 6)) break;
+  }
+}
+
+__device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
+  const int S = p.stages;
+  const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
+  const uint32_t idesc = idesc_bf16(BM, p.N, p.a_mn, p.b_mn);
+  const uint32_t idesc_db = idesc_bf16(BM, 16, p.a_mn, false);
+  // an all-ones 16 x 16 BF16 block, no swizzle: every layout reads ones
+  const uint64_t ones = smem_desc(smem_u32(s.ones), 128, 256, 0);
+  uint32_t it = 0, lt = 0;
+  const int n_tiles = p.m_tiles * p.splits;
+  bool ok = true;
+  for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++lt) {
+    int mt, sp, nk;
+    long long k0;
+    tile_range(p, t, mt, sp, k0, nk);
+    uint32_t ab = lt % n_acc, ar = lt / n_acc;
+    if (!mbar_wait(&s.tempty[ab], (ar & 1) ^ 1, p.err, 2)) break;
+    tc_fence_after();
+    uint32_t d = tbase + ab * (uint32_t)acc_stride(p);
+    for (int kb = 0; kb < nk; ++kb, ++it) {
+      uint32_t st = it % S, rd = it / S;
+      if (!mbar_wait(&s.full[st], rd & 1, p.err, 3)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint32_t aa = smem_u32(s.a + (size_t)st * p.a_bytes);
+      uint32_t ba = smem_u32(s.b + (size_t)st * p.b_bytes);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k) {
+        // K-major: the next 16 elements of K are 32 bytes further along
+        // each swizzled 128-byte row; MN-major: 16 more rows of 128 bytes.
+        uint64_t adesc = p.a_mn ? smem_desc(aa + 2048 * k, 8192, 1024, kSwizzle128)
+                                : smem_desc(aa + 32 * k, 16, 1024, kSwizzle128);
+        uint64_t bdesc = p.b_mn ? smem_desc(ba + 2048 * k, 8192, 1024, kSwizzle128)
+                                : smem_desc(ba + 32 * k, 16, 1024, kSwizzle128);
+        uint32_t acc = (kb | k) != 0;
+        mma_bf16(d, adesc, bdesc, idesc, acc);
+        if (p.with_db) mma_bf16(d + p.N, adesc, ones, idesc_db, acc);
+      }
+      mma_commit(&s.empty[st]);
+    }
+    if (ok) mma_commit(&s.tfull[ab]);
+  }
+  // all MMAs of this thread must have completed before TMEM is freed
+  mma_commit(s.drain);
+  mbar_wait(s.drain, 0, p.err, 4);
+}
+
+__device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int q = warp & 3;  // TMEM lane quadrant this warp may access
+  const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
+  const int n_tiles = p.m_tiles * p.splits;
+  uint32_t lt = 0;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+    int mt, sp, nk;
+    long long k0;
+    tile_range(p, t, mt, sp, k0, nk);
+    uint32_t ab = lt % n_acc, ar = lt / n_acc;
+    if (!mbar_wait(&s.tfull[ab], ar & 1, p.err, 5)) return;
+    tc_fence_after();
+    const int row = mt * BM + q * 32 + lane;
+    const bool live = row < p.M;
+    const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)acc_stride(p);
+    float dot = 0.0f;
+    for (int c0 = 0; c0 < p.N; c0 += 32) {
+      float v[32];
+      tmem_ld32(trow + c0, v);
+      if (!live) continue;
+      if (p.epi == kTcFwd) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          int c = c0 + i;
+          float x = v[i] + (c < p.n_store ? p.bias[c] : 0.0f);
+          x = fmaxf(x, 0.0f);
+          v[i] = x;
+          if (p.w_out && c < p.n_store) dot = fmaf(x, p.w_out[c], dot);
+        }
+      } else if (p.epi == kTcDx) {
+        const uint4 *h = reinterpret_cast<const uint4 *>(p.hprev + (long long)row * p.ldh + c0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint4 u = h[j];
+          uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            // a BF16 value is > 0 iff its sign bit is clear and it is not +0
+            uint32_t lo = w[e] & 0xFFFFu, hi = w[e] >> 16;
+            if (!(lo != 0 && (lo & 0x8000u) == 0)) v[8 * j + 2 * e] = 0.0f;
+            if (!(hi != 0 && (hi & 0x8000u) == 0)) v[8 * j + 2 * e + 1] = 0.0f;
+          }
+        }
+      }
+      if (p.epi == kTcFwd || p.epi == kTcDx) {
+        if (c0 + 32 <= p.n_store) {
+          uint4 *o = reinterpret_cast<uint4 *>(p.out + (long long)row * p.ldo + c0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            o[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]), pack_bf16(v[8 * j + 2], v[8 * j + 3]),
+                              pack_bf16(v[8 * j + 4], v[8 * j + 5]),
+                              pack_bf16(v[8 * j + 6], v[8 * j + 7]));
+        } else {
+          for (int i = 0; i < 32 && c0 + i < p.n_store; ++i)
+            p.out[(long long)row * p.ldo + c0 + i] = __float2bfloat16_rn(v[i]);
+        }
+      } else {
+        float *o = p.part + ((long long)sp * p.M + row) * p.part_ld + c0;
+        for (int i = 0; i < 32 && c0 + i < p.n_store; ++i) o[i] = v[i];
+      }
+    }
+    if (p.epi == kTcDw && p.with_db) {
+      float v[32];
+      tmem_ld32(trow + p.N, v);   // 16 db columns (all equal) + padding
+      if (live) p.part_db[(long long)sp * p.M + row] = v[0];
+    }
+    if (p.epi == kTcFwd && p.z_out && live) p.z_out[row] = dot + p.b_out[0];
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&s.tempty[ab]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+              const TcGemmArgs p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  Smem s = carve(base, p);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(n_acc * acc_stride(p))) cols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < p.stages; ++i) {
+      mbar_init(&s.full[i], 1);
+      mbar_init(&s.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&s.tfull[i], 1);
+      mbar_init(&s.tempty[i], 4);
+    }
+    mbar_init(s.drain, 1);
+    fence_mbar_init();
+  }
+  if (p.with_db) {
+    uint32_t *o = reinterpret_cast<uint32_t *>(s.ones);
+    for (int i = threadIdx.x; i < kOnesBytes / 4; i += blockDim.x) o[i] = 0x3F803F80u;  // 1.0, 1.0
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(s.tslot, cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *s.tslot;
+
+  if (warp == 0) {
+    if (lane == 0) producer(&ta, &tb, p, s);
+  } else if (warp == 1) {
+    if (lane == 0) mma_issuer(p, s, tbase);
+  } else {
+    epilogue(p, s, tbase);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, cols);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+}  // namespace
+
+bool make_tmap_bf16(CUtensorMap *tm, const void *ptr, long long rows, long long cols,
+                    long long ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, TcGemmArgs a, int num_sms,
+                   cudaStream_t st) {
+  a.a_bytes = BM * BK * 2;  // 128 rows x 128 bytes, or 2 MN-major boxes of 64 x 128 bytes
+  a.b_bytes = a.b_mn ? ((a.N + 63) / 64) * 8192 : a.N * BK * 2;
+  const int fixed = kOnesBytes + 1024 /*alignment*/ + 256 /*barriers*/;
+  const int budget = 220 * 1024;
+  int stages = (budget - fixed) / (a.a_bytes + a.b_bytes);
+  a.stages = stages > 8 ? 8 : stages;
+  if (a.stages < 2) return (int)cudaErrorInvalidValue;
+  size_t smem = (size_t)a.stages * (a.a_bytes + a.b_bytes) + fixed;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  int tiles = a.m_tiles * a.splits;
+  int grid = tiles < num_sms ? tiles : num_sms;
+  k_tc_gemm<<<grid, kThreads, smem, st>>>(ta, tb, a);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace dinr

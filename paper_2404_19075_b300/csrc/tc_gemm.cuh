@@ -1,0 +1,59 @@
+// Persistent tcgen05 BF16 GEMM with the MLP's fused epilogues.
+//
+// D[M x N] = sum_k A(m, k) B(n, k) with BF16 operands fetched by TMA into
+// 128-byte-swizzled shared memory and FP32 accumulation in TMEM.
+//   A K-major: A(m, k) = A[m][k] (rows of samples), tile 128 x 64
+//   A MN-major: A(m, k) = A[k][m] (e.g. delta^T for weight gradients)
+//   B K-major: B(n, k) = B[n][k]; B MN-major: B(n, k) = B[k][n]
+// N <= 256 and a multiple of 16 (one N tile per CTA), M tiles of 128 rows,
+// K in blocks of 64 (TMA zero-fills past the tensor's extent).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace dinr {
+
+enum TcEpi {
+  kTcFwd = 0,  // out = bf16(act(acc + bias)); optional z_out = out . w_out + b_out
+  kTcDx = 1,   // out = bf16(acc * [hprev > 0])
+  kTcDw = 2    // part[split][m][n] = acc (FP32); optional part_db[split][m] = sum over k of A
+};
+
+struct TcGemmArgs {
+  int epi;
+  int M, N;              // output rows / columns (MMA N)
+  long long K;           // reduction extent
+  int a_mn, b_mn;
+  int m_tiles, splits;
+  long long k_per_split; // multiple of 64
+  int n_store;           // columns written (<= N)
+  // kTcFwd
+  const float *bias;
+  __nv_bfloat16 *out;
+  long long ldo;
+  const float *w_out, *b_out;
+  float *z_out;
+  // kTcDx
+  const __nv_bfloat16 *hprev;
+  long long ldh;
+  // kTcDw
+  float *part, *part_db;
+  long long part_ld;
+  int with_db;
+  // launch geometry (filled by the launcher)
+  int stages, a_bytes, b_bytes;
+  int *err;              // device flag: nonzero when a bounded wait gave up
+};
+
+// 2D BF16 tensor map over a row-major [rows][cols] array with row stride
+// ld (elements), box {64, box_rows}, 128-byte swizzle, zero fill.
+bool make_tmap_bf16(CUtensorMap *tm, const void *ptr, long long rows, long long cols,
+                    long long ld, int box_rows);
+
+// Launches over min(tiles, SMs) persistent CTAs. Returns a cudaError_t.
+int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, TcGemmArgs a, int num_sms,
+                   cudaStream_t st);
+
+}  // namespace dinr

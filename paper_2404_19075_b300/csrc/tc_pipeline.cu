@@ -1,14 +1,372 @@
+// BF16 tensor-core pipeline of the training step and the queries.
+//
+// Per pass of rays: encode (BF16 features) -> H forward GEMMs with fused
+// bias + ReLU (the last one also forms z_out = h . w_out + b_out) ->
+// warp-segmented forward model + loss -> output-layer delta -> per layer
+// from the last: split-K weight-gradient GEMM (bias gradient from an
+// all-ones MMA in the same kernel) and the input-gradient GEMM with the ReLU
+// mask fused. Master weights, gradients, segment sums and loss stay FP32.
 #include "tc.cuh"
+#include "tc_gemm.cuh"
 
-bool tc_supported(const dinr_net *) { return false; }
-long long tc_bytes_per_sample(const dinr_ctx *) { return 0; }
-dinr_status tc_alloc(dinr_ctx *) { return DINR_ERR_UNSUPPORTED; }
-void tc_destroy(dinr_ctx *) {}
-dinr_status tc_params_changed(dinr_ctx *) { return DINR_OK; }
-dinr_status tc_loss_grad(dinr_ctx *, int) { return DINR_ERR_UNSUPPORTED; }
-dinr_status tc_forward_rays(dinr_ctx *, const dinr::SourceArgs &, long long, int, float *) {
-  return DINR_ERR_UNSUPPORTED;
+#include <vector>
+
+using namespace dinr;
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "%s: %s (%s:%d)", #call,        \
+                                    cudaGetErrorString(e_), __FILE__, __LINE__);      \
+  } while (0)
+#define CKL()            \
+  do {                   \
+    ++c->launches;       \
+    CK(cudaGetLastError()); \
+  } while (0)
+
+namespace {
+
+constexpr int kMaxSplits = 148;
+
+struct TcState {
+  int num_sms = 148;
+  std::vector<__nv_bfloat16 *> Wb, WbT;  // per hidden layer: [fan_out][kpad], [fan_in][W]
+  std::vector<int> kpad;
+  __nv_bfloat16 *E = nullptr, *H = nullptr, *D0 = nullptr, *D1 = nullptr;
+  float *zout = nullptr, *dz = nullptr, *ray_l = nullptr, *ray_p = nullptr, *pbar = nullptr,
+        *sq = nullptr, *part = nullptr, *part_db = nullptr;
+  long long part_floats = 0;
+  int *err = nullptr;
+};
+
+TcState *S_(dinr_ctx *c) { return static_cast<TcState *>(c->tc); }
+
+// ------------------------------------------------------------ small kernels
+
+__global__ void k_to_bf16(const float *W, int rows, int cols, int kpad, __nv_bfloat16 *Wb,
+                          __nv_bfloat16 *WbT) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= (long long)rows * kpad) return;
+  int r = (int)(q / kpad), k = (int)(q - (long long)r * kpad);
+  float x = k < cols ? W[(long long)r * cols + k] : 0.0f;
+  __nv_bfloat16 b = __float2bfloat16_rn(x);
+  Wb[q] = b;
+  if (WbT && k < cols) WbT[(long long)k * rows + r] = b;
 }
-dinr_status tc_forward_points(dinr_ctx *, const dinr::SourceArgs &, long long, float *) {
-  return DINR_ERR_UNSUPPORTED;
+
+// delta_H[s][c] = dz[s] * w_out[c] * [h_H[s][c] > 0]
+__global__ void k_out_delta_bf16(const float *dz, const float *w_out, const __nv_bfloat16 *h,
+                                 int W, long long n, __nv_bfloat16 *D) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n * W) return;
+  long long s = q / W;
+  int col = (int)(q - s * W);
+  float x = __bfloat162float(h[q]);
+  D[q] = __float2bfloat16_rn(x > 0.0f ? dz[s] * w_out[col] : 0.0f);
+}
+
+// part[z][c] = sum over rows of split z of w[s] * h[s][c] (blocked summation)
+__global__ void k_colsum_bf16(const __nv_bfloat16 *X, int C, long long rows, const float *w,
+                              int splits, float *part) {
+  int z = blockIdx.y;
+  long long per = (rows + splits - 1) / splits;
+  long long r0 = z * per, r1 = r0 + per < rows ? r0 + per : rows;
+  for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < C; col += gridDim.x * blockDim.x) {
+    float acc = 0.0f, blk = 0.0f;
+    for (long long r = r0; r < r1; ++r) {
+      blk += w[r] * __bfloat162float(X[r * C + col]);
+      if (((r - r0) & 255) == 255) {
+        acc += blk;
+        blk = 0.0f;
+      }
+    }
+    part[(long long)z * C + col] = acc + blk;
+  }
+}
+
+int splits_for(long long rows, int m_tiles, int num_sms) {
+  long long s = num_sms / m_tiles;
+  long long by_rows = (rows + 4095) / 4096;  // at least 4096 samples per split
+  if (s > by_rows) s = by_rows;
+  if (s > kMaxSplits) s = kMaxSplits;
+  return (int)(s < 1 ? 1 : s);
+}
+
+dinr_status gemm(dinr_ctx *c, const char *name, double flops, double bytes, TcGemmArgs a,
+                 const void *A, long long a_rows, long long a_cols, const void *B,
+                 long long b_rows, long long b_cols) {
+  CUtensorMap ta, tb;
+  int a_box = a.a_mn ? 64 : 128;
+  int b_box = a.b_mn ? 64 : a.N;
+  if (!make_tmap_bf16(&ta, A, a_rows, a_cols, a_cols, a_box) ||
+      !make_tmap_bf16(&tb, B, b_rows, b_cols, b_cols, b_box))
+    return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "tensor map encoding failed (%s)", name);
+  a.err = S_(c)->err;
+  ProfScope ps(c, name, flops, bytes);
+  int e = launch_tc_gemm(ta, tb, a, S_(c)->num_sms, c->st);
+  ++c->launches;
+  if (e != 0)
+    return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "%s launch: %s", name,
+                                  cudaGetErrorString((cudaError_t)e));
+  return DINR_OK;
+}
+
+__nv_bfloat16 *hid(dinr_ctx *c, int L, long long ns) {
+  return S_(c)->H + (long long)L * ns * c->W;
+}
+
+// Forward chain over ns samples whose features are in E.
+dinr_status forward(dinr_ctx *c, long long ns) {
+  TcState *t = S_(c);
+  for (int L = 0; L < c->H; ++L) {
+    TcGemmArgs a{};
+    a.epi = kTcFwd;
+    a.M = (int)ns;
+    a.N = c->W;
+    a.K = t->kpad[L];
+    a.m_tiles = (int)((ns + 127) / 128);
+    a.splits = 1;
+    a.k_per_split = (a.K + 63) / 64 * 64;
+    a.n_store = c->W;
+    a.bias = c->d_params + c->offb[L];
+    a.out = hid(c, L, ns);
+    a.ldo = c->W;
+    if (L == c->H - 1) {
+      a.w_out = c->d_params + c->offW[c->H];
+      a.b_out = c->d_params + c->offb[c->H];
+      a.z_out = t->zout;
+    }
+    const void *A = L == 0 ? (const void *)t->E : (const void *)hid(c, L - 1, ns);
+    long long acols = L == 0 ? c->ldE : c->W;
+    dinr_status s = gemm(c, "tc_fwd", 2.0 * ns * c->W * c->fan_in[L],
+                         2.0 * ns * (acols + c->W), a, A, ns, acols, t->Wb[L], c->W, t->kpad[L]);
+    if (s != DINR_OK) return s;
+  }
+  return DINR_OK;
+}
+
+dinr_status reduce_into(dinr_ctx *c, const float *part, int splits, long long C, long long off,
+                        bool acc) {
+  launch_reduce_partials(part, splits, C, c->d_grad + off, acc, c->st);
+  CKL();
+  return DINR_OK;
+}
+
+dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
+  TcState *t = S_(c);
+  const int W = c->W;
+  __nv_bfloat16 *hH = hid(c, c->H - 1, ns);
+  // output layer: delta_H, grad w_out = sum dz h_H, grad b_out = sum dz
+  k_out_delta_bf16<<<ceil_div(ns * W, 256), 256, 0, c->st>>>(t->dz, c->d_params + c->offW[c->H],
+                                                             hH, W, ns, t->D0);
+  CKL();
+  int cs = colsum_splits(ns);
+  k_colsum_bf16<<<dim3(ceil_div(W, 256), cs), 256, 0, c->st>>>(hH, W, ns, t->dz, cs, t->part);
+  CKL();
+  dinr_status s = reduce_into(c, t->part, cs, W, c->offW[c->H], acc);
+  if (s != DINR_OK) return s;
+  launch_colsum(t->dz, 1, 1, ns, nullptr, false, 0, cs, t->part, c->st);
+  CKL();
+  s = reduce_into(c, t->part, cs, 1, c->offb[c->H], acc);
+  if (s != DINR_OK) return s;
+
+  __nv_bfloat16 *D = t->D0, *Dn = t->D1;
+  for (int L = c->H - 1; L >= 0; --L) {
+    const void *In = L == 0 ? (const void *)t->E : (const void *)hid(c, L - 1, ns);
+    int in_cols = L == 0 ? c->ldE : W;
+    int fan_in = c->fan_in[L];
+    TcGemmArgs a{};
+    a.epi = kTcDw;
+    a.M = W;
+    a.N = in_cols;
+    a.K = ns;
+    a.a_mn = 1;
+    a.b_mn = 1;
+    a.m_tiles = (W + 127) / 128;
+    a.splits = splits_for(ns, a.m_tiles, t->num_sms);
+    a.k_per_split = ((ns + a.splits - 1) / a.splits + 63) / 64 * 64;
+    a.splits = (int)((ns + a.k_per_split - 1) / a.k_per_split);
+    a.n_store = fan_in;
+    a.part = t->part;
+    a.part_ld = fan_in;
+    a.part_db = t->part_db;
+    a.with_db = 1;
+    s = gemm(c, "tc_dw", 2.0 * ns * W * fan_in, 2.0 * ns * (W + in_cols), a, D, ns, W, In, ns,
+             in_cols);
+    if (s != DINR_OK) return s;
+    s = reduce_into(c, t->part, a.splits, (long long)W * fan_in, c->offW[L], acc);
+    if (s != DINR_OK) return s;
+    s = reduce_into(c, t->part_db, a.splits, W, c->offb[L], acc);
+    if (s != DINR_OK) return s;
+    if (L > 0) {
+      TcGemmArgs b{};
+      b.epi = kTcDx;
+      b.M = (int)ns;
+      b.N = W;
+      b.K = W;
+      b.m_tiles = (int)((ns + 127) / 128);
+      b.splits = 1;
+      b.k_per_split = (W + 63) / 64 * 64;
+      b.n_store = W;
+      b.out = Dn;
+      b.ldo = W;
+      b.hprev = hid(c, L - 1, ns);
+      b.ldh = W;
+      s = gemm(c, "tc_dx", 2.0 * ns * W * W, 2.0 * ns * 3 * W, b, D, ns, W, t->WbT[L], W, W);
+      if (s != DINR_OK) return s;
+      __nv_bfloat16 *tmp = D;
+      D = Dn;
+      Dn = tmp;
+    }
+  }
+  return DINR_OK;
+}
+
+dinr_status check_err(dinr_ctx *c) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, S_(c)->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (e) {
+    CK(cudaMemsetAsync(S_(c)->err, 0, sizeof(int), c->st));
+    return (dinr_status)dinr_fail(c, DINR_ERR_TIMEOUT,
+                                  "a tensor-core kernel gave up waiting (code %d)", e);
+  }
+  return DINR_OK;
+}
+
+}  // namespace
+
+bool tc_supported(const dinr_net *net) {
+  // ReLU hidden layers; widths in [32, 256], multiples of 32 (one N tile,
+  // whole 32-column TMEM loads); at most 16 octaves (<= 144 padded inputs).
+  return net->act == DINR_ACT_RELU && net->width % 32 == 0 && net->width >= 32 &&
+         net->width <= 256 && net->n_freq <= 16;
+}
+
+long long tc_bytes_per_sample(const dinr_ctx *c) {
+  return 2LL * (c->ldE + (long long)(c->H + 2) * c->W) + 8 + 16;
+}
+
+dinr_status tc_alloc(dinr_ctx *c) {
+  TcState *t = new TcState();
+  c->tc = t;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  long long ns = (long long)c->chunk_rays * c->S;
+  auto grab = [&](void **p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    c->allocs.push_back(*p);
+    return true;
+  };
+  bool ok = true;
+  for (int L = 0; L < c->H; ++L) {
+    int kp = L == 0 ? c->ldE : c->W;
+    t->kpad.push_back(kp);
+    void *wb = nullptr, *wt = nullptr;
+    ok = ok && grab(&wb, sizeof(__nv_bfloat16) * (size_t)c->W * kp);
+    ok = ok && grab(&wt, sizeof(__nv_bfloat16) * (size_t)c->fan_in[L] * c->W);
+    t->Wb.push_back((__nv_bfloat16 *)wb);
+    t->WbT.push_back((__nv_bfloat16 *)wt);
+  }
+  int maxN = c->ldE > c->W ? c->ldE : c->W;
+  long long pf = (long long)kMaxSplits * c->W * maxN;
+  long long pc = (long long)colsum_splits(ns) * c->W;
+  t->part_floats = pf > pc ? pf : pc;
+  ok = ok && grab((void **)&t->E, 2ull * ns * c->ldE) &&
+       grab((void **)&t->H, 2ull * ns * c->W * c->H) && grab((void **)&t->D0, 2ull * ns * c->W) &&
+       grab((void **)&t->D1, 2ull * ns * c->W) && grab((void **)&t->zout, 4ull * ns) &&
+       grab((void **)&t->dz, 4ull * ns) && grab((void **)&t->ray_l, 4ull * ns) &&
+       grab((void **)&t->ray_p, 4ull * ns) && grab((void **)&t->pbar, 4ull * ns) &&
+       grab((void **)&t->sq, 4ull * ns) && grab((void **)&t->part, 4ull * t->part_floats) &&
+       grab((void **)&t->part_db, 4ull * kMaxSplits * c->W) && grab((void **)&t->err, 16);
+  if (!ok) return (dinr_status)dinr_fail(c, DINR_ERR_OOM, "BF16 workspace allocation failed");
+  CK(cudaMemsetAsync(t->err, 0, 16, c->st));
+  return tc_params_changed(c);
+}
+
+void tc_destroy(dinr_ctx *c) {
+  delete S_(c);
+  c->tc = nullptr;
+}
+
+dinr_status tc_params_changed(dinr_ctx *c) {
+  TcState *t = S_(c);
+  if (!t) return DINR_OK;
+  for (int L = 0; L < c->H; ++L) {
+    int rows = c->W, cols = c->fan_in[L], kp = t->kpad[L];
+    k_to_bf16<<<ceil_div((long long)rows * kp, 256), 256, 0, c->st>>>(
+        c->d_params + c->offW[L], rows, cols, kp, t->Wb[L], t->WbT[L]);
+    CKL();
+  }
+  return DINR_OK;
+}
+
+dinr_status tc_loss_grad(dinr_ctx *c, int n) {
+  TcState *t = S_(c);
+  float inv_B = 1.0f / (float)n;
+  for (int r0 = 0, pass = 0; r0 < n; r0 += c->chunk_rays, ++pass) {
+    int nr = n - r0 < c->chunk_rays ? n - r0 : c->chunk_rays;
+    long long ns = (long long)nr * c->S;
+    SourceArgs src{};
+    src.kind = kSrcTrainRays;
+    src.idx = c->d_idx + r0;
+    {
+      ProfScope ps(c, "encode", 0.0, 2.0 * ns * c->ldE);
+      launch_encode_bf16(c->geo, src, nr, c->S, c->F, c->ldE, t->E, t->ray_l, c->d_proj,
+                         t->ray_p, c->st);
+      CKL();
+    }
+    dinr_status s = forward(c, ns);
+    if (s != DINR_OK) return s;
+    launch_segsum(t->zout, c->out_act, nr, c->S, c->mu0, t->ray_l, t->ray_p, inv_B, true,
+                  t->pbar, t->sq, t->dz, c->st);
+    CKL();
+    launch_loss_sum(t->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
+    CKL();
+    s = backward(c, ns, pass > 0);
+    if (s != DINR_OK) return s;
+  }
+  return DINR_OK;
+}
+
+static dinr_status tc_forward(dinr_ctx *c, const SourceArgs &src0, long long n_rays, int S,
+                              float *out) {
+  TcState *t = S_(c);
+  long long per = (long long)c->chunk_rays * c->S / S;
+  if (per < 1) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "S larger than the workspace");
+  for (long long r0 = 0; r0 < n_rays; r0 += per) {
+    long long nr = n_rays - r0 < per ? n_rays - r0 : per;
+    SourceArgs src = src0;
+    if (src.kind == kSrcTrainRays)
+      src.idx = src0.idx + r0;
+    else
+      src.first = src0.first + r0;
+    long long ns = nr * S;
+    launch_encode_bf16(c->geo, src, nr, S, c->F, c->ldE, t->E, t->ray_l, nullptr, nullptr,
+                       c->st);
+    CKL();
+    dinr_status s = forward(c, ns);
+    if (s != DINR_OK) return s;
+    launch_segsum(t->zout, c->out_act, nr, S, c->mu0, t->ray_l, nullptr, 1.0f, false, out + r0,
+                  nullptr, nullptr, c->st);
+    CKL();
+  }
+  return DINR_OK;
+}
+
+dinr_status tc_poll(dinr_ctx *c) { return S_(c) ? check_err(c) : DINR_OK; }
+
+dinr_status tc_forward_rays(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S,
+                            float *out) {
+  return tc_forward(c, src, n_rays, S, out);
+}
+
+dinr_status tc_forward_points(dinr_ctx *c, const SourceArgs &src, long long n, float *out) {
+  return tc_forward(c, src, n, 1, out);
 }

@@ -1,0 +1,126 @@
+"""GPU parity of the BF16 tensor-core path (tcgen05 GEMMs, FP32
+accumulation) against the FP64 oracle through the C ABI. Tolerance for the
+BF16 path: 2e-2, norm-wise relative per tensor and element-wise relative to
+the tensor's largest magnitude."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import step as ostep
+from synthetic import workloads as wl
+
+from gpu_util import assert_close, make_model, rel_err, require_gpu, split_grad
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-2
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _grad_check(g_gpu, g_or, net, tol):
+    for L, ((gw, gb), (ow, ob)) in enumerate(zip(split_grad(g_gpu, net), split_grad(g_or, net))):
+        assert_close(gw, ow, tol, f"dW layer {L}")
+        assert_close(gb, ob, tol, f"db layer {L}")
+
+
+@pytest.fixture(scope="module")
+def c1():
+    w = wl.workload(1)
+    idx = wl.ray_subset(w.geom.n_proj, 1024, w.seeds["sampler"])
+    m, theta, proj = make_model(w, "bf16", idx=idx)
+    ref = ostep.loss_and_grad(theta, w.geom, w.net, idx, proj.astype(np.float64))
+    yield w, m, theta, proj, idx, ref
+    m.close()
+
+
+def test_c1_forward_model_bf16(c1):
+    w, m, theta, proj, idx, ref = c1
+    assert_close(m.predict(idx).cpu().numpy(), ref["p_bar"], TOL, "p_bar")
+
+
+def test_c1_loss_and_gradient_bf16(c1):
+    w, m, theta, proj, idx, ref = c1
+    loss, grad = m.loss_grad(idx)
+    assert abs(loss.item() - ref["loss"]) <= TOL * ref["loss"]
+    _grad_check(grad.cpu().numpy(), ref["grad"], w.net, TOL)
+
+
+def test_c1_deterministic_bf16(c1):
+    w, m, theta, proj, idx, ref = c1
+    l1, g1 = m.loss_grad(idx)
+    l2, g2 = m.loss_grad(idx)
+    assert l1.item() == l2.item() and torch.equal(g1, g2)
+
+
+def test_c1_ragged_batches_bf16(c1):
+    w, m, theta, proj, idx, ref = c1
+    for n in (1, 5, 129):
+        sub = idx[:n]
+        r = ostep.loss_and_grad(theta, w.geom, w.net, sub, proj.astype(np.float64))
+        loss, grad = m.loss_grad(sub)
+        assert abs(loss.item() - r["loss"]) <= TOL * r["loss"] + 1e-9
+        assert_close(grad.cpu().numpy(), r["grad"], TOL, f"n={n}")
+
+
+def test_c1_train_step_bf16(c1):
+    w, m, theta, proj, idx, ref = c1
+    st = m.get_state()
+    loss = m.train_step(idx)
+    assert abs(loss - ref["loss"]) <= TOL * ref["loss"]
+    out = ostep.train_step(theta, np.zeros_like(theta), np.zeros_like(theta), 1, w.geom, w.net,
+                           w.train, idx, proj.astype(np.float64))
+    d_gpu = m.params().cpu().numpy() - theta
+    d_or = out["theta"] - theta
+    big = np.abs(out["grad"]) > 1e-2 * np.abs(out["grad"]).max()
+    assert rel_err(d_gpu[big], d_or[big]) <= 5e-2
+    m.set_state(st)
+
+
+def test_c1_queries_bf16(c1):
+    w, m, theta, proj, idx, ref = c1
+    g, net = w.geom, w.net
+    rng = np.random.default_rng(3)
+    coords = np.stack([rng.uniform(0, 1, 300), rng.uniform(-1, 1, 300),
+                       rng.uniform(-0.7, 0.7, 300), rng.uniform(-0.7, 0.7, 300)], 1)
+    coords = coords.astype(np.float32).astype(np.float64)
+    assert_close(m.query(coords).cpu().numpy(), ostep.query(theta, g, net, coords), TOL, "query")
+    img = m.project(1.1, 0.3, 20, 24, 40).cpu().numpy()
+    assert_close(img, ostep.project_view(theta, g, net, 1.1, 0.3, 20, 24, 40), TOL, "project")
+
+
+@pytest.mark.parametrize("c,n", [(2, 128), (3, 64)])
+def test_subset_parity_bf16(c, n):
+    w = wl.workload(c)
+    idx = wl.ray_subset(w.geom.n_proj, n, 99)
+    m, theta, proj = make_model(w, "bf16", idx=idx, batch=n)
+    ref = ostep.loss_and_grad(theta, w.geom, w.net, idx, proj.astype(np.float64))
+    assert_close(m.predict(idx).cpu().numpy(), ref["p_bar"], TOL, "p_bar")
+    loss, grad = m.loss_grad(idx)
+    assert abs(loss.item() - ref["loss"]) <= TOL * ref["loss"]
+    _grad_check(grad.cpu().numpy(), ref["grad"], w.net, TOL)
+    m.close()
+
+
+def test_bf16_matches_fp32_path_full_batch_c2():
+    """At the full 65,536-ray batch of the parallel-beam workload the two
+    library paths agree (the FP32 path is within 1e-5 of the oracle on
+    subsets), checked on p_bar of the whole batch and on the gradient."""
+    from paper_2404_19075_b300 import phantom_project
+    w = wl.workload(2)
+    proj = phantom_project(w.geom, wl.phantom(w))
+    th = wl.he_init(w.net, w.seeds["weights"]).astype(np.float32)
+    idx = torch.as_tensor(wl.ray_subset(w.geom.n_proj, 65536, 5), device="cuda")
+    from paper_2404_19075_b300 import Dinr
+    out = {}
+    for prec in ("fp32", "bf16"):
+        m = Dinr(w.geom, w.net, w.train, proj, prec=prec, init_params=th)
+        p = m.predict(idx).cpu().numpy()
+        loss, grad = m.loss_grad(idx)
+        out[prec] = (p, loss.item(), grad.cpu().numpy())
+        m.close()
+    assert_close(out["bf16"][0], out["fp32"][0], TOL, "p_bar")
+    assert abs(out["bf16"][1] - out["fp32"][1]) <= TOL * out["fp32"][1]
+    _grad_check(out["bf16"][2], out["fp32"][2], w.net, TOL)
