@@ -94,19 +94,49 @@ def out_act_grad(z, kind):
     raise ValueError(kind)
 
 
-def forward(theta, net, e):
-    """M(r; gamma) for encoded inputs e [n, d_in]. Returns (M [n], cache)."""
+def round_bf16(x):
+    """Round to the nearest BF16 value (8 significant bits, ties to even),
+    returned as float64. Used only to take ReLU decisions in BF16."""
+    f = np.asarray(x, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def relu_decisions_bf16(theta, net, e):
+    """Which hidden units are active, decided the way a BF16 tensor-core
+    forward decides them: operands (features, weights, activations) rounded
+    to BF16, products summed in FP32, bias added in FP32. Returns one
+    boolean mask per hidden layer. (A ReLU mask is an integer decided by
+    floating point; to compare a BF16 path with this oracle both take that
+    decision in BF16, while every value stays FP64.)"""
+    layers = unpack(theta, net)
+    h = round_bf16(e).astype(np.float32)
+    masks = []
+    for W, b in layers[:-1]:
+        z = h @ round_bf16(W).astype(np.float32).T + np.asarray(b, np.float32)
+        masks.append(z > 0)
+        h = round_bf16(np.maximum(z, 0)).astype(np.float32)
+    return masks
+
+
+def forward(theta, net, e, masks=None):
+    """M(r; gamma) for encoded inputs e [n, d_in]. Returns (M [n], cache).
+    masks: optional ReLU decisions per hidden layer (default: z > 0)."""
     layers = unpack(theta, net)
     h = np.asarray(e, np.float64)
     hs, zs = [h], []
-    for W, b in layers[:-1]:
+    for k, (W, b) in enumerate(layers[:-1]):
         z = h @ W.T + b
-        h = act(z, net.act)
+        if masks is not None:
+            h = np.where(masks[k], z, 0.0)
+        else:
+            h = act(z, net.act)
         zs.append(z)
         hs.append(h)
     w_out, b_out = layers[-1]
     z_out = h @ w_out[0] + b_out[0]
-    return out_act(z_out, net.out_act), dict(hs=hs, zs=zs, z_out=z_out)
+    return out_act(z_out, net.out_act), dict(hs=hs, zs=zs, z_out=z_out, masks=masks)
 
 
 def backward(theta, net, cache, dM):
@@ -124,7 +154,10 @@ def backward(theta, net, cache, dM):
     grads[-1] = (np.outer(np.ones(1), dz @ hs[-1]), np.array([dz.sum()]))
     up = np.outer(dz, w_out[0])
     for k in range(len(layers) - 2, -1, -1):
-        delta = up * act_grad(zs[k], net.act)
+        if cache.get("masks") is not None:
+            delta = up * cache["masks"][k]
+        else:
+            delta = up * act_grad(zs[k], net.act)
         grads[k] = (delta.T @ hs[k], delta.sum(axis=0))
         if k > 0:
             up = delta @ layers[k][0]

@@ -41,12 +41,15 @@ def loss(p_bar, p):
     return float(np.mean(r * r))
 
 
-def loss_and_grad(theta, geom, net, idx, proj):
+def loss_and_grad(theta, geom, net, idx, proj, decide=None):
     """Loss of Eq. 5 and its gradient (Appendix A, "partiald") for the
-    minibatch idx against the projection stack proj (flat, length MN)."""
+    minibatch idx against the projection stack proj (flat, length MN).
+    decide="bf16" takes the ReLU decisions in BF16 (see
+    network.relu_decisions_bf16); all values are FP64 either way."""
     S, B = geom.samples_per_ray, len(idx)
     e, l = encoded_samples(geom, net, idx)
-    M, cache = network.forward(theta, net, e)
+    masks = network.relu_decisions_bf16(theta, net, e) if decide == "bf16" else None
+    M, cache = network.forward(theta, net, e, masks)
     M = M.reshape(B, S)
     p = np.asarray(proj, np.float64)[np.asarray(idx)]
     p_bar = forward_model(M, l, S, geom.mu0)

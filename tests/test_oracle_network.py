@@ -198,3 +198,33 @@ def test_query_matches_network_at_sample_points():
     rbar = np.stack([2 * coords[:, 0] - 1, coords[:, 1], coords[:, 2], coords[:, 3]], 1)
     M, _ = network.forward(theta, net, network.encode(rbar, net.n_freq))
     assert np.allclose(step.query(theta, g, net, coords), g.mu0 * M)
+
+
+# ------------------------------------------- BF16 decisions (comparison aid)
+
+def test_round_bf16_definition():
+    """Round to nearest with 8 significant bits, ties to even."""
+    vals = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -9, -2.5,
+                     1.0 + 2.0 ** -7 + 2.0 ** -8, 3.0e38])
+    want = np.array([1.0, 1.0, 1.0 + 2.0 ** -6, 1.0, -2.5, 1.0 + 2.0 ** -6, 2.9980e38])
+    got = network.round_bf16(vals)
+    assert np.array_equal(got[:6], want[:6])
+    assert abs(got[6] / 3.0e38 - 1) < 2 ** -8
+
+
+def test_bf16_decisions_only_change_near_kinks():
+    """Deciding ReLUs in BF16 changes the network only where a
+    pre-activation is within BF16 rounding of zero; with all decisions equal
+    to z > 0 the FP64 results are unchanged."""
+    g, net, theta, idx = _small(B=48)
+    e, l = step.encoded_samples(g, net, idx)
+    masks = network.relu_decisions_bf16(theta, net, e)
+    _, cache = network.forward(theta, net, e)
+    for k, z in enumerate(cache["zs"]):
+        differ = masks[k] != (z > 0)
+        assert differ.mean() < 0.01
+        assert np.all(np.abs(z[differ]) < 0.05 * np.abs(z).max())
+    exact = [z > 0 for z in cache["zs"]]
+    M1, _ = network.forward(theta, net, e, exact)
+    M0, _ = network.forward(theta, net, e)
+    assert np.array_equal(M1, M0)
