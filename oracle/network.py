@@ -103,29 +103,21 @@ def round_bf16(x):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def relu_decisions(theta, net, e, precision):
-    """Which hidden units are active, decided in a lower precision:
-      "bf16": operands (features, weights, activations) rounded to BF16,
-              products summed in FP32, bias added in FP32 (a BF16 tensor-core
-              forward);
-      "fp32": everything in FP32 (an FP32 forward).
-    Returns one boolean mask per hidden layer. A ReLU mask is an integer
-    decided by floating point; to compare a reduced-precision path with this
-    oracle both take that decision in the path's precision, while every
-    value the oracle computes stays FP64."""
+def relu_decisions_bf16(theta, net, e):
+    """Which hidden units are active, decided the way a BF16 tensor-core
+    forward decides them: operands (features, weights, activations) rounded
+    to BF16, products summed in FP32, bias added in FP32. Returns one
+    boolean mask per hidden layer. (A ReLU mask is an integer decided by
+    floating point; to compare a BF16 path with this oracle both take that
+    decision in BF16, while every value stays FP64.)"""
     layers = unpack(theta, net)
-    rnd = round_bf16 if precision == "bf16" else (lambda x: np.asarray(x, np.float64))
-    h = rnd(e).astype(np.float32)
+    h = round_bf16(e).astype(np.float32)
     masks = []
     for W, b in layers[:-1]:
-        z = h @ rnd(W).astype(np.float32).T + np.asarray(b, np.float32)
+        z = h @ round_bf16(W).astype(np.float32).T + np.asarray(b, np.float32)
         masks.append(z > 0)
-        h = rnd(np.maximum(z, 0)).astype(np.float32)
+        h = round_bf16(np.maximum(z, 0)).astype(np.float32)
     return masks
-
-
-def relu_decisions_bf16(theta, net, e):
-    return relu_decisions(theta, net, e, "bf16")
 
 
 def forward(theta, net, e, masks=None):

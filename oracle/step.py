@@ -44,11 +44,11 @@ def loss(p_bar, p):
 def loss_and_grad(theta, geom, net, idx, proj, decide=None):
     """Loss of Eq. 5 and its gradient (Appendix A, "partiald") for the
     minibatch idx against the projection stack proj (flat, length MN).
-    decide="bf16" or "fp32" takes the ReLU decisions in that precision (see
-    network.relu_decisions); all values are FP64 either way."""
+    decide="bf16" takes the ReLU decisions in BF16 (see
+    network.relu_decisions_bf16); all values are FP64 either way."""
     S, B = geom.samples_per_ray, len(idx)
     e, l = encoded_samples(geom, net, idx)
-    masks = network.relu_decisions(theta, net, e, decide) if decide else None
+    masks = network.relu_decisions_bf16(theta, net, e) if decide == "bf16" else None
     M, cache = network.forward(theta, net, e, masks)
     M = M.reshape(B, S)
     p = np.asarray(proj, np.float64)[np.asarray(idx)]

@@ -1,9 +1,7 @@
 """GPU parity of the plain FP32 path against the FP64 oracle, called through
 the C ABI. Tolerance for the FP32 path: 1e-5, norm-wise relative per tensor
 and element-wise relative to the tensor's largest magnitude; integer work
-(indices, sampler) bit-exact. Gradients are compared with the oracle's ReLU
-decisions taken in FP32 (a ReLU mask is an integer decided by floating point;
-both sides decide it in the kernel's precision, values stay FP64)."""
+(indices, sampler) bit-exact."""
 import math
 
 import numpy as np
@@ -62,7 +60,7 @@ def c1():
     w = wl.workload(1)
     idx = wl.ray_subset(w.geom.n_proj, 1024, w.seeds["sampler"])
     m, theta, proj = make_model(w, "fp32", idx=idx)
-    ref = ostep.loss_and_grad(theta, w.geom, w.net, idx, proj.astype(np.float64), decide="fp32")
+    ref = ostep.loss_and_grad(theta, w.geom, w.net, idx, proj.astype(np.float64))
     yield w, m, theta, proj, idx, ref
     m.close()
 
@@ -120,7 +118,7 @@ def test_c1_ragged_and_single_ray_batches(c1):
     w, m, theta, proj, idx, ref = c1
     for n in (1, 7, 333):
         sub = idx[:n]
-        r = ostep.loss_and_grad(theta, w.geom, w.net, sub, proj.astype(np.float64), decide="fp32")
+        r = ostep.loss_and_grad(theta, w.geom, w.net, sub, proj.astype(np.float64))
         loss, grad = m.loss_grad(sub)
         assert abs(loss.item() - r["loss"]) <= TOL * r["loss"] + 1e-12
         assert_close(grad.cpu().numpy(), r["grad"], TOL, f"n={n}")
@@ -191,7 +189,7 @@ def test_subset_parity_fp32(c, n):
     w = wl.workload(c)
     idx = wl.ray_subset(w.geom.n_proj, n, 99)
     m, theta, proj = make_model(w, "fp32", idx=idx, batch=n)
-    ref = ostep.loss_and_grad(theta, w.geom, w.net, idx, proj.astype(np.float64), decide="fp32")
+    ref = ostep.loss_and_grad(theta, w.geom, w.net, idx, proj.astype(np.float64))
     assert_close(m.predict(idx).cpu().numpy(), ref["p_bar"], TOL, "p_bar")
     loss, grad = m.loss_grad(idx)
     assert abs(loss.item() - ref["loss"]) <= TOL * ref["loss"]
