@@ -18,6 +18,7 @@ One JSON line is printed by rank 0.
 from __future__ import annotations
 
 import argparse
+from dataclasses import replace
 import json
 import math
 import os
@@ -195,6 +196,8 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     w = wl.workload(WORKLOAD)
+    if args.rays:
+        w = replace(w, train=replace(w.train, batch_rays=args.rays))
     g, net = w.geom, w.net
     B, S = w.train.batch_rays, g.samples_per_ray
     proj = phantom_project(g, wl.phantom(w))            # measurements, resident in HBM
@@ -310,6 +313,9 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rays", type=int, default=0,
+                    help="rays per step (default: the workload's 65,536); smaller batches "
+                         "are for profiler captures, not bench lines")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -67,12 +67,12 @@ __global__ void __launch_bounds__(256) k_sgemm(SgemmArgs a) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
 
-  // Weight-gradient sums run over many thousands of samples: accumulate
-  // blocks of kBlockK samples separately and add each block into the total
-  // (blocked summation keeps the rounding growth near kBlockK + K/kBlockK
-  // instead of K).
-  constexpr bool kBlocked = (EPI == kEpiPartial);
-  constexpr int kBlockK = 256;
+  // Blocked summation: products are accumulated in blocks of kBlockK terms
+  // and each block is added into the total, which keeps the rounding growth
+  // near kBlockK + K/kBlockK instead of K (K is 256 for hidden layers and
+  // thousands of samples for weight gradients).
+  constexpr bool kBlocked = true;
+  constexpr int kBlockK = 32;
   float tot[kBlocked ? 8 : 1][kBlocked ? 8 : 1];
 #pragma unroll
   for (int i = 0; i < (kBlocked ? 8 : 1); ++i)
