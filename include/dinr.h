@@ -228,6 +228,34 @@ DINR_API dinr_status dinr_phantom_project(const dinr_geometry *geom, int n_ell,
                                  double growth, const int64_t *idx_dev,
                                  int64_t n, float *out_dev, void *cuda_stream);
 
+/* The projection of dinr_phantom_project, for callers that cannot allocate
+ * device memory. dinr_phantom_project stages its geometry table and
+ * ellipsoid parameters in device memory it allocates on every call; some
+ * callers must not do that, for example a host application whose device
+ * memory is owned by its own pool allocator under a fixed budget, or a
+ * latency-bound loop that cannot afford cudaMalloc/cudaFree and the device
+ * synchronisation that cudaFree implies. This variant stages the same data in
+ * one static device array instead and calls no cudaMalloc, cudaFree or any
+ * other allocating routine. The paper has no counterpart: it is a property
+ * of this library, not of the method.
+ *   Limits: n_views <= 4096 and n_ell <= 1024, otherwise DINR_ERR_ARG. The
+ *   array (320 KiB) lives on every GPU that loads the library until the
+ *   process exits.
+ *   The first call on a device looks the array's device address up (once
+ *   per device, with that device current); make that first call before any
+ *   stream capture.
+ *   All calls on a device share the array, which keeps the last call's
+ *   contents: calls whose work overlaps on the GPU (for example on two
+ *   streams at once) race and give wrong results; serialise them.
+ *   Arguments, output and errors as dinr_phantom_project, except that the
+ *   call does not wait for the stream: out_dev is ready when the stream
+ *   reaches the end of the call's work. */
+DINR_API dinr_status dinr_phantom_project_noalloc(const dinr_geometry *geom, int n_ell,
+                                                  const double *centre, const double *axes,
+                                                  const double *rho, const double *vel,
+                                                  double growth, const int64_t *idx_dev,
+                                                  int64_t n, float *out_dev, void *cuda_stream);
+
 /* Per-kernel timing of the context's own launches with CUDA events on its
  * stream (tracing; no counterpart in the paper). dinr_profile(ctx, 1)
  * clears and starts recording, 0 stops. dinr_profile_report waits for the

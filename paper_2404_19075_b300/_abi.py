@@ -70,6 +70,8 @@ PROTOTYPES = {
     "dinr_sample_indices": (C.c_int, [vp, i64, C.c_int, vp]),
     "dinr_phantom_project": (C.c_int, [C.POINTER(Geometry), C.c_int, vp, vp, vp, vp,
                                        C.c_double, vp, i64, vp, vp]),
+    "dinr_phantom_project_noalloc": (C.c_int, [C.POINTER(Geometry), C.c_int, vp, vp, vp, vp,
+                                               C.c_double, vp, i64, vp, vp]),
     "dinr_profile": (C.c_int, [vp, C.c_int]),
     "dinr_profile_report": (C.c_int, [vp, C.c_char_p, C.c_size_t]),
     "dinr_synchronize": (C.c_int, [vp]),
