@@ -138,55 +138,161 @@ __device__ __forceinline__ void source_coords(const GeoDev &g, const SourceArgs 
   }
 }
 
-template <typename T>
-__device__ __forceinline__ T to_t(float x);
-template <>
-__device__ __forceinline__ float to_t<float>(float x) { return x; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_t<__nv_bfloat16>(float x) {
-  return __float2bfloat16_rn(x);
+// Features of one coordinate at octaves 0..F-1 into sc[2F] (sin, cos).
+// kFast (BF16 path): exact sincospif at octaves 0, 4, 8, ..., and angle
+// doubling in between (sin 2a = 2 sin a cos a, cos 2a = (cos a - sin a)
+// (cos a + sin a)); three doublings grow the error to about 1e-6, far below
+// BF16 resolution. Otherwise every octave uses the exact reduction.
+template <bool kFast>
+__device__ __forceinline__ void coord_features(double c, int F, float *sc) {
+  if (!kFast) {
+    octave_features(c, F, sc);
+    return;
+  }
+  float hi = (float)c;
+  float lo = (float)(c - (double)hi);
+  float scale = 1.0f, sp = 0.0f, cp = 1.0f;
+  for (int l = 0; l < F; ++l) {
+    if ((l & 3) == 0) {
+      float a = hi * scale;
+      float n = 2.0f * rintf(0.5f * a);
+      float y = (a - n) + lo * scale;
+      sincospif(y, &sp, &cp);
+    } else {
+      float s2 = 2.0f * sp * cp;
+      cp = (cp - sp) * (cp + sp);
+      sp = s2;
+    }
+    sc[2 * l] = sp;
+    sc[2 * l + 1] = cp;
+    scale *= 2.0f;
+  }
 }
 
-// One thread per sample. ray_l receives the chord length of each ray (1 for
-// point sources, so that the forward model reduces to mu0 * M); ray_p the
-// measured projection of each training ray.
 template <typename T>
-__global__ void k_encode(GeoDev g, SourceArgs src, long long n_rays, int S, int F, int ld,
-                         T *E, float *ray_l, const float *proj, float *ray_p) {
-  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= n_rays * S) return;
-  long long r = q / S;
-  int j = (int)(q - r * S);
-  double c[4];
-  float len = 0.0f;
-  source_coords(g, src, r, j, S, c, &len);
-  T *row = E + q * ld;
-  for (int k = 0; k < 4; ++k) row[k] = to_t<T>((float)c[k]);
-  float sc[2 * kMaxFreq];
-  for (int k = 0; k < 4; ++k) {
-    octave_features(c[k], F, sc);
-    for (int l = 0; l < 2 * F; ++l) row[4 + 2 * F * k + l] = to_t<T>(sc[l]);
+struct FeatWriter;
+// FP32 rows: one 32-bit word per feature.
+template <>
+struct FeatWriter<float> {
+  static constexpr int kPerWord = 1;
+  __device__ static void put(uint32_t *row, int f, float a, float b) {
+    row[f] = __float_as_uint(a);
+    row[f + 1] = __float_as_uint(b);
   }
-  for (int k = 4 + 8 * F; k < ld; ++k) row[k] = to_t<T>(0.0f);
-  if (j == 0) {
-    if (ray_l) ray_l[r] = len;
-    if (ray_p) ray_p[r] = proj ? proj[src.idx[r]] : 0.0f;
+};
+// BF16 rows: one 32-bit word per pair of adjacent features.
+template <>
+struct FeatWriter<__nv_bfloat16> {
+  static constexpr int kPerWord = 2;
+  __device__ static void put(uint32_t *row, int f, float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    row[f >> 1] = *reinterpret_cast<uint32_t *>(&v);
   }
+};
+
+constexpr int kEncThreads = 128;
+
+// One block encodes kEncThreads consecutive samples. The rays they belong
+// to are set up once each (FP64) into shared memory, together with the
+// time features of the ray (constant along it); each thread then forms its
+// sample's row of features in shared memory, and the block writes its rows,
+// which are contiguous in E, with coalesced 32-bit stores. ray_l receives
+// each ray's chord length (1 for point sources, so that the forward model
+// reduces to mu0 * M); ray_p the measured value of each training ray.
+template <typename T, bool kFast>
+__global__ void __launch_bounds__(kEncThreads)
+    k_encode(GeoDev g, SourceArgs src, long long n_rays, int S, int F, int ld, T *E,
+             float *ray_l, const float *proj, float *ray_p) {
+  extern __shared__ uint32_t enc_smem[];
+  __shared__ Ray rays[kEncThreads];
+  __shared__ float tfeat[kEncThreads][2 * kMaxFreq];
+  const int words = ld * (int)sizeof(T) / 4;
+  const int stride = words + 1;  // odd stride: conflict-free row writes
+  const long long n = n_rays * S;
+  const long long q0 = (long long)blockIdx.x * kEncThreads;
+  const int tid = threadIdx.x;
+  const bool ray_src = src.kind == kSrcTrainRays || src.kind == kSrcVirtualView;
+  const long long r_first = q0 / S;
+  long long q_last = q0 + kEncThreads - 1 < n - 1 ? q0 + kEncThreads - 1 : n - 1;
+  const int nr_blk = (int)(q_last / S - r_first + 1);
+
+  if (ray_src && tid < nr_blk) {
+    long long r = r_first + tid;
+    Ray ray = source_ray(g, src, r);
+    rays[tid] = ray;
+    coord_features<kFast>(ray.tbar, F, tfeat[tid]);
+    if (r * S >= q0) {  // the block holding the ray's first sample reports it
+      if (ray_l) ray_l[r] = (float)ray.l;
+      if (ray_p) ray_p[r] = proj ? proj[src.idx[r]] : 0.0f;
+    }
+  }
+  __syncthreads();
+
+  const long long q = q0 + tid;
+  uint32_t *row = enc_smem + tid * stride;
+  if (q < n) {
+    long long r = q / S;
+    int j = (int)(q - r * S);
+    double c[4];
+    float sc[2 * kMaxFreq];
+    if (ray_src) {
+      int k = (int)(r - r_first);
+      c[0] = rays[k].tbar;
+      sample_coords(g, rays[k], j, S, c[1], c[2], c[3]);
+      for (int l = 0; l < 2 * F; ++l) sc[l] = tfeat[k][l];
+    } else {
+      float len;
+      source_coords(g, src, r, j, S, c, &len);
+      if (ray_l) ray_l[r] = 1.0f;
+      coord_features<kFast>(c[0], F, sc);
+    }
+    FeatWriter<T>::put(row, 0, (float)c[0], (float)c[1]);
+    FeatWriter<T>::put(row, 2, (float)c[2], (float)c[3]);
+    for (int l = 0; l < F; ++l) FeatWriter<T>::put(row, 4 + 2 * l, sc[2 * l], sc[2 * l + 1]);
+    for (int k = 1; k < 4; ++k) {
+      coord_features<kFast>(c[k], F, sc);
+      for (int l = 0; l < F; ++l)
+        FeatWriter<T>::put(row, 4 + 2 * F * k + 2 * l, sc[2 * l], sc[2 * l + 1]);
+    }
+    for (int f = 4 + 8 * F; f < ld; f += 2) FeatWriter<T>::put(row, f, 0.0f, 0.0f);
+  }
+  __syncthreads();
+
+  const long long rows = q_last - q0 + 1;
+  uint32_t *dst = reinterpret_cast<uint32_t *>(E + q0 * ld);
+  for (long long w = tid; w < rows * words; w += kEncThreads) {
+    int rr = (int)(w / words), cc = (int)(w - (long long)rr * words);
+    dst[w] = enc_smem[rr * stride + cc];
+  }
+}
+
+template <typename T, bool kFast>
+static void launch_encode(const GeoDev &g, const SourceArgs &src, long long n_rays, int S, int F,
+                          int ld, T *E, float *ray_l, const float *proj, float *ray_p,
+                          cudaStream_t st) {
+  long long n = n_rays * S;
+  int words = ld * (int)sizeof(T) / 4;
+  size_t smem = (size_t)kEncThreads * (words + 1) * 4;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_encode<T, kFast>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         96 * 1024);
+    attr = true;
+  }
+  k_encode<T, kFast><<<ceil_div(n, kEncThreads), kEncThreads, smem, st>>>(g, src, n_rays, S, F,
+                                                                         ld, E, ray_l, proj,
+                                                                         ray_p);
 }
 
 void launch_encode_f32(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
                        int F, int ld, float *E, float *ray_l, const float *proj,
                        float *ray_p, cudaStream_t st) {
-  long long n = n_rays * S;
-  k_encode<float><<<ceil_div(n, 128), 128, 0, st>>>(g, src, n_rays, S, F, ld, E, ray_l, proj,
-                                                     ray_p);
+  launch_encode<float, false>(g, src, n_rays, S, F, ld, E, ray_l, proj, ray_p, st);
 }
 void launch_encode_bf16(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
                         int F, int ld, __nv_bfloat16 *E, float *ray_l, const float *proj,
                         float *ray_p, cudaStream_t st) {
-  long long n = n_rays * S;
-  k_encode<__nv_bfloat16><<<ceil_div(n, 128), 128, 0, st>>>(g, src, n_rays, S, F, ld, E, ray_l,
-                                                             proj, ray_p);
+  launch_encode<__nv_bfloat16, true>(g, src, n_rays, S, F, ld, E, ray_l, proj, ray_p, st);
 }
 
 // ------------------------------------- output layer, forward model, loss

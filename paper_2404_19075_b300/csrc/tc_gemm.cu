@@ -1,9 +1,11 @@
 // Persistent warp-specialised tcgen05 GEMM (see tc_gemm.cuh).
 //
-// Roles per CTA (192 threads, one CTA per SM):
+// Roles per CTA (320 threads, one CTA per SM):
 //   warp 0      one thread issues TMA loads into an S-stage shared ring
 //   warp 1      allocates TMEM; one thread issues tcgen05.mma (K = 16 each)
-//   warps 2..5  epilogue: TMEM -> registers -> fused op -> global memory
+//   warps 2..9  epilogue: TMEM -> registers -> fused op -> global memory;
+//               two warps per TMEM lane quadrant take alternate 32-column
+//               chunks
 // Accumulators are double-buffered in TMEM when they fit, so the epilogue
 // of one tile overlaps the MMAs of the next. Every mbarrier wait is bounded
 // in time; a timeout sets *err and the roles wind down without hanging.
@@ -18,12 +20,14 @@ using namespace tc;
 
 namespace {
 constexpr int BM = 128, BK = 64;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
 constexpr int kOnesBytes = 1024;
 
 struct Smem {
   uint8_t *a, *b, *ones;
-  uint64_t *full, *empty, *tfull, *tempty, *drain;
+  float *dot;  // [2 tile parities][2 halves][128 rows]
+  uint64_t *full, *empty, *tfull, *tempty, *drain, *dotbar;
   uint32_t *tslot;
 };
 
@@ -32,12 +36,14 @@ __device__ __forceinline__ Smem carve(uint8_t *base, const TcGemmArgs &p) {
   s.a = base;
   s.b = base + (size_t)p.stages * p.a_bytes;
   s.ones = s.b + (size_t)p.stages * p.b_bytes;
-  s.full = reinterpret_cast<uint64_t *>(s.ones + kOnesBytes);
+  s.dot = reinterpret_cast<float *>(s.ones + kOnesBytes);
+  s.full = reinterpret_cast<uint64_t *>(s.dot + 2 * 2 * 128);
   s.empty = s.full + p.stages;
   s.tfull = s.empty + p.stages;
   s.tempty = s.tfull + 2;
   s.drain = s.tempty + 2;
-  s.tslot = reinterpret_cast<uint32_t *>(s.drain + 1);
+  s.dotbar = s.drain + 1;
+  s.tslot = reinterpret_cast<uint32_t *>(s.dotbar + 2);
   return s;
 }
 
@@ -149,74 +155,104 @@ __device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
   mbar_wait(s.drain, 0, p.err, 4);
 }
 
+__device__ __forceinline__ void load_h32(const __nv_bfloat16 *p, uint4 (&h)[4]) {
+  const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) h[j] = q[j];
+}
+
+__device__ __forceinline__ bool bf16_positive(uint32_t b) { return b != 0 && (b & 0x8000u) == 0; }
+
 __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int q = warp & 3;  // TMEM lane quadrant this warp may access
+  const int q = warp & 3;              // TMEM lane quadrant this warp may access
+  const int half = (warp - 2) / 4;     // which alternate 32-column chunks
   const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
   const int n_tiles = p.m_tiles * p.splits;
+  const int n_chunks = (p.N + 31) / 32;
   uint32_t lt = 0;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
     int mt, sp, nk;
     long long k0;
     tile_range(p, t, mt, sp, k0, nk);
     uint32_t ab = lt % n_acc, ar = lt / n_acc;
+    const int r_in = q * 32 + lane;
+    const int row = mt * BM + r_in;
+    const bool live = row < p.M;
+    // prefetch the mask operand of this warp's first chunk
+    uint4 hcur[4], hnext[4];
+    if (p.epi == kTcDx && live && half < n_chunks)
+      load_h32(p.hprev + (long long)row * p.ldh + half * 32, hcur);
     if (!mbar_wait(&s.tfull[ab], ar & 1, p.err, 5)) return;
     tc_fence_after();
-    const int row = mt * BM + q * 32 + lane;
-    const bool live = row < p.M;
     const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)acc_stride(p);
     float dot = 0.0f;
-    for (int c0 = 0; c0 < p.N; c0 += 32) {
+    for (int ch = half; ch < n_chunks; ch += 2) {
+      const int c0 = ch * 32;
+      if (p.epi == kTcDx && live && ch + 2 < n_chunks)
+        load_h32(p.hprev + (long long)row * p.ldh + c0 + 64, hnext);
       float v[32];
       tmem_ld32(trow + c0, v);
-      if (!live) continue;
-      if (p.epi == kTcFwd) {
+      if (live) {
+        if (p.epi == kTcFwd) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          int c = c0 + i;
-          float x = v[i] + (c < p.n_store ? p.bias[c] : 0.0f);
-          x = fmaxf(x, 0.0f);
-          v[i] = x;
-          if (p.w_out && c < p.n_store) dot = fmaf(x, p.w_out[c], dot);
-        }
-      } else if (p.epi == kTcDx) {
-        const uint4 *h = reinterpret_cast<const uint4 *>(p.hprev + (long long)row * p.ldh + c0);
+          for (int i = 0; i < 32; ++i) {
+            int c = c0 + i;
+            float x = fmaxf(v[i] + (c < p.n_store ? p.bias[c] : 0.0f), 0.0f);
+            v[i] = x;
+            if (p.w_out && c < p.n_store) dot = fmaf(x, p.w_out[c], dot);
+          }
+        } else if (p.epi == kTcDx) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          uint4 u = h[j];
-          uint32_t w[4] = {u.x, u.y, u.z, u.w};
+          for (int j = 0; j < 4; ++j) {
+            uint32_t w[4] = {hcur[j].x, hcur[j].y, hcur[j].z, hcur[j].w};
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            // a BF16 value is > 0 iff its sign bit is clear and it is not +0
-            uint32_t lo = w[e] & 0xFFFFu, hi = w[e] >> 16;
-            if (!(lo != 0 && (lo & 0x8000u) == 0)) v[8 * j + 2 * e] = 0.0f;
-            if (!(hi != 0 && (hi & 0x8000u) == 0)) v[8 * j + 2 * e + 1] = 0.0f;
+            for (int e = 0; e < 4; ++e) {
+              if (!bf16_positive(w[e] & 0xFFFFu)) v[8 * j + 2 * e] = 0.0f;
+              if (!bf16_positive(w[e] >> 16)) v[8 * j + 2 * e + 1] = 0.0f;
+            }
           }
         }
-      }
-      if (p.epi == kTcFwd || p.epi == kTcDx) {
-        if (c0 + 32 <= p.n_store) {
-          uint4 *o = reinterpret_cast<uint4 *>(p.out + (long long)row * p.ldo + c0);
+        if (p.epi == kTcFwd || p.epi == kTcDx) {
+          if (c0 + 32 <= p.n_store) {
+            uint4 *o = reinterpret_cast<uint4 *>(p.out + (long long)row * p.ldo + c0);
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            o[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]), pack_bf16(v[8 * j + 2], v[8 * j + 3]),
-                              pack_bf16(v[8 * j + 4], v[8 * j + 5]),
-                              pack_bf16(v[8 * j + 6], v[8 * j + 7]));
+            for (int j = 0; j < 4; ++j)
+              o[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]),
+                                pack_bf16(v[8 * j + 2], v[8 * j + 3]),
+                                pack_bf16(v[8 * j + 4], v[8 * j + 5]),
+                                pack_bf16(v[8 * j + 6], v[8 * j + 7]));
+          } else {
+            for (int i = 0; i < 32 && c0 + i < p.n_store; ++i)
+              p.out[(long long)row * p.ldo + c0 + i] = __float2bfloat16_rn(v[i]);
+          }
         } else {
-          for (int i = 0; i < 32 && c0 + i < p.n_store; ++i)
-            p.out[(long long)row * p.ldo + c0 + i] = __float2bfloat16_rn(v[i]);
+          float *o = p.part + ((long long)sp * p.M + row) * p.part_ld + c0;
+          for (int i = 0; i < 32 && c0 + i < p.n_store; ++i) o[i] = v[i];
         }
-      } else {
-        float *o = p.part + ((long long)sp * p.M + row) * p.part_ld + c0;
-        for (int i = 0; i < 32 && c0 + i < p.n_store; ++i) o[i] = v[i];
+      }
+      if (p.epi == kTcDx) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hcur[j] = hnext[j];
       }
     }
-    if (p.epi == kTcDw && p.with_db) {
+    if (p.epi == kTcDw && p.with_db && half == 0) {
       float v[32];
-      tmem_ld32(trow + p.N, v);   // 16 db columns (all equal) + padding
+      tmem_ld32(trow + p.N, v);  // 16 db columns (all equal) + padding
       if (live) p.part_db[(long long)sp * p.M + row] = v[0];
     }
-    if (p.epi == kTcFwd && p.z_out && live) p.z_out[row] = dot + p.b_out[0];
+    if (p.epi == kTcFwd && p.z_out) {
+      // the second half hands its partial dot products to the first half
+      float *db = s.dot + (ab & 1) * 256;
+      if (half == 1) {
+        db[r_in] = dot;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s.dotbar[ab]);
+      } else {
+        if (!mbar_wait(&s.dotbar[ab], ar & 1, p.err, 7)) return;
+        if (live) p.z_out[row] = dot + db[r_in] + p.b_out[0];
+      }
+    }
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&s.tempty[ab]);
@@ -242,9 +278,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&s.tfull[i], 1);
-      mbar_init(&s.tempty[i], 4);
+      mbar_init(&s.tempty[i], kEpiWarps);
     }
     mbar_init(s.drain, 1);
+    for (int i = 0; i < 2; ++i) mbar_init(&s.dotbar[i], kEpiWarps / 2);
     fence_mbar_init();
   }
   if (p.with_db) {
@@ -305,7 +342,7 @@ int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, TcGemmArgs a, i
                    cudaStream_t st) {
   a.a_bytes = BM * BK * 2;  // 128 rows x 128 bytes, or 2 MN-major boxes of 64 x 128 bytes
   a.b_bytes = a.b_mn ? ((a.N + 63) / 64) * 8192 : a.N * BK * 2;
-  const int fixed = kOnesBytes + 1024 /*alignment*/ + 256 /*barriers*/;
+  const int fixed = kOnesBytes + 2048 /*dot buffer*/ + 1024 /*alignment*/ + 256 /*barriers*/;
   const int budget = 220 * 1024;
   int stages = (budget - fixed) / (a.a_bytes + a.b_bytes);
   a.stages = stages > 8 ? 8 : stages;
