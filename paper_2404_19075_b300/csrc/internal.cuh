@@ -29,6 +29,46 @@ struct SourceArgs {
   double gtbar;
 };
 
+// The ray of ray slot r for each ray source kind.
+__device__ __forceinline__ Ray source_ray(const GeoDev &g, const SourceArgs &s, long long r) {
+  if (s.kind == kSrcTrainRays) return make_ray(g, s.idx[r]);
+  long long q = s.first + r;
+  int row = (int)(q / s.vcols), col = (int)(q - (long long)row * s.vcols);
+  double u = g.ou + (col + 0.5) * s.vpu, v = g.ov + (row + 0.5) * s.vpv;
+  return ray_at(g, u, v, s.vc, s.vs, s.vtbar);
+}
+
+// Normalised (t, z, y, x) of sample j of ray/point slot r.
+__device__ __forceinline__ void source_coords(const GeoDev &g, const SourceArgs &s,
+                                              long long r, int j, int S, double c[4],
+                                              float *len) {
+  if (s.kind == kSrcTrainRays || s.kind == kSrcVirtualView) {
+    Ray ray = source_ray(g, s, r);
+    c[0] = ray.tbar;
+    sample_coords(g, ray, j, S, c[1], c[2], c[3]);
+    *len = (float)ray.l;
+  } else if (s.kind == kSrcPoints) {
+    const float *p = s.points + 4 * (s.first + r);
+    c[0] = (double)p[0] * s.t_scale + s.t_bias;
+    c[1] = (double)p[1] * g.zs + g.zb;
+    c[2] = (double)p[2] * g.inv_R;
+    c[3] = (double)p[3] * g.inv_R;
+    *len = 1.0f;
+  } else {
+    long long nx = s.gdims[0], ny = s.gdims[1], q = s.first + r;
+    long long iz = q / (nx * ny), rem = q - iz * nx * ny;
+    long long iy = rem / nx, ix = rem - iy * nx;
+    double x = s.glo[0] + (ix + 0.5) * s.gstep[0];
+    double y = s.glo[1] + (iy + 0.5) * s.gstep[1];
+    double z = s.glo[2] + (iz + 0.5) * s.gstep[2];
+    c[0] = s.gtbar;
+    c[1] = z * g.zs + g.zb;
+    c[2] = y * g.inv_R;
+    c[3] = x * g.inv_R;
+    *len = 1.0f;
+  }
+}
+
 // Encoded features of a pass. Rays r in [0, n_rays) own samples
 // [r*S, r*S + S) (S = 1 for point sources). Features are written as
 // FP32 or BF16 [n_samples][ld] with zero padding from d_in to ld.

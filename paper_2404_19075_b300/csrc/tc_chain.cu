@@ -1,0 +1,372 @@
+// Fused forward chain (see tc_chain.cuh).
+//
+// One persistent CTA per SM, 320 threads:
+//   warp 0      one thread streams the weight K-chunks of every layer by TMA
+//               into an S-stage ring (each chunk once per tile)
+//   warp 1      TMEM owner; one thread issues tcgen05.mma (M = 128, N = W,
+//               K = 16) for every layer of two 128-sample tiles in turn
+//   warps 2..9  two per TMEM lane quadrant: build the layer-0 input of a
+//               tile in shared memory (ray generation + Fourier features,
+//               Sec. III, App. A, App. B), then after each layer read the
+//               accumulator, add the bias, apply ReLU, write the BF16
+//               activations back into the tile's shared buffer (the next
+//               layer's A operand) and TMA-store them to HBM for the
+//               backward; after the last layer they form
+//               z_out = h . w_out + b_out.
+// The two tiles ping-pong: while the epilogue warps work on one, the tensor
+// cores run the other. Activations of a tile never leave the SM between
+// layers. All mbarrier waits are bounded (see tc_ptx.cuh).
+#include "tc_chain.cuh"
+#include "tc_ptx.cuh"
+
+namespace dinr {
+
+using namespace tc;
+
+namespace {
+
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kChunkBytes = 128 * 128;  // 128 rows x 64 BF16 (one K-chunk, 128B swizzle)
+constexpr int kSmemLimit = 232448;
+
+struct Smem {
+  uint8_t *A[2];      // two tile slots, K-chunks of kChunkBytes each
+  uint8_t *ring;      // weight stages, W rows x 128 bytes each
+  float *dot;         // [2 slots][128] partial output dot products
+  uint64_t *full, *empty, *aready, *tfull, *dotbar, *drain;
+  uint32_t *tslot;
+};
+
+__host__ __device__ inline int a_chunks(int W, int k0) { return (W > k0 ? W : k0) / 64; }
+
+__device__ __forceinline__ Smem carve(uint8_t *base, const ChainArgs &p) {
+  Smem s;
+  const size_t a_bytes = (size_t)a_chunks(p.W, p.k0) * kChunkBytes;
+  s.A[0] = base;
+  s.A[1] = base + a_bytes;
+  s.ring = base + 2 * a_bytes;
+  s.dot = reinterpret_cast<float *>(s.ring + (size_t)p.stages * p.W * 128);
+  s.full = reinterpret_cast<uint64_t *>(s.dot + 2 * 128);
+  s.empty = s.full + p.stages;
+  s.aready = s.empty + p.stages;
+  s.tfull = s.aready + 2;
+  s.dotbar = s.tfull + 2;
+  s.drain = s.dotbar + 2;
+  s.tslot = reinterpret_cast<uint32_t *>(s.drain + 1);
+  return s;
+}
+
+// Byte offset of 16-byte unit c16 of row r in a 128B-swizzled K-chunk.
+__device__ __forceinline__ uint32_t swz(int r, int c16) {
+  return (uint32_t)(r * 128 + ((c16 ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Tiles of this CTA: blockIdx.x + k * gridDim.x, processed in pairs.
+__device__ __forceinline__ long long tile_of(const ChainArgs &p, int pair, int slot) {
+  return (long long)blockIdx.x + (long long)(2 * pair + slot) * gridDim.x;
+}
+__device__ __forceinline__ int n_pairs(const ChainArgs &p) {
+  int nt = (p.m_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  return (nt + 1) / 2;
+}
+
+__device__ __forceinline__ int layer_k(const ChainArgs &p, int L) { return L == 0 ? p.k0 : p.W; }
+
+// ---------------------------------------------------------------- roles
+
+__device__ void producer(const ChainMaps &maps, const ChainArgs &p, const Smem &s) {
+  for (int L = 0; L < p.H; ++L) prefetch_tmap(&maps.w[L]);
+  const uint32_t S = p.stages, tx = (uint32_t)p.W * 128;
+  uint32_t it = 0;
+  const int np = n_pairs(p);
+  for (int pr = 0; pr < np; ++pr)
+    for (int L = 0; L < p.H; ++L)
+      for (int slot = 0; slot < 2; ++slot)
+        for (int kc = 0; kc < layer_k(p, L) / 64; ++kc, ++it) {
+          uint32_t st = it % S, rd = it / S;
+          if (!mbar_wait(&s.empty[st], (rd & 1) ^ 1, p.err, 11)) goto drain;
+          mbar_expect_tx(&s.full[st], tx);
+          tma_load_2d(&maps.w[L], &s.full[st], s.ring + (size_t)st * p.W * 128, 64 * kc, 0);
+        }
+drain:
+  uint32_t n = it < S ? it : S;
+  for (uint32_t q = it - n; q < it; ++q)
+    if (!mbar_wait(&s.full[q % S], (q / S) & 1, p.err, 16)) break;
+}
+
+__device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
+  const uint32_t S = p.stages;
+  const uint32_t idesc = idesc_bf16(128, p.W, false, false);
+  uint32_t it = 0, waits[2] = {0, 0};
+  const int np = n_pairs(p);
+  bool ok = true;
+  for (int pr = 0; pr < np && ok; ++pr)
+    for (int L = 0; L < p.H && ok; ++L)
+      for (int slot = 0; slot < 2 && ok; ++slot) {
+        if (!mbar_wait(&s.aready[slot], waits[slot]++ & 1, p.err, 12)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tbase + (uint32_t)(slot * p.W);
+        const uint32_t a0 = smem_u32(s.A[slot]);
+        const int nk = layer_k(p, L) / 64;
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          uint32_t st = it % S, rd = it / S;
+          if (!mbar_wait(&s.full[st], rd & 1, p.err, 13)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t b0 = smem_u32(s.ring + (size_t)st * p.W * 128);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            uint64_t ad = smem_desc(a0 + kc * kChunkBytes + 32 * k, 16, 1024, kSwizzle128);
+            uint64_t bd = smem_desc(b0 + 32 * k, 16, 1024, kSwizzle128);
+            mma_bf16(d, ad, bd, idesc, (kc | k) != 0);
+          }
+          mma_commit(&s.empty[st]);
+        }
+        if (ok) mma_commit(&s.tfull[slot]);
+      }
+  mma_commit(s.drain);
+  mbar_wait(s.drain, 0, p.err, 14);
+}
+
+// Layer-0 input of one tile: the Fourier features of its 128 samples, in
+// the K-chunks this warp owns (chunks half, half + 2, ...).
+__device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *A,
+                            long long tile, int q, int half, int lane) {
+  const int r_in = q * 32 + lane;
+  const long long smp = tile * 128 + r_in;
+  const bool live = smp < p.ns;
+  const bool ray_src = p.src.kind == kSrcTrainRays || p.src.kind == kSrcVirtualView;
+  double c[4] = {0.0, 0.0, 0.0, 0.0};
+  if (ray_src) {
+    long long r = (live ? smp : 0) / p.S;
+    int j = (int)((live ? smp : 0) - r * p.S);
+    Ray ray;
+    const long long warp0 = tile * 128 + q * 32;
+    if (p.S % 32 == 0) {
+      // the warp's 32 consecutive samples lie on one ray: set it up once
+      if (lane == 0 && warp0 < p.ns) ray = source_ray(p.g, p.src, warp0 / p.S);
+      double *rd = reinterpret_cast<double *>(&ray);
+#pragma unroll
+      for (int k = 0; k < (int)(sizeof(Ray) / sizeof(double)); ++k)
+        rd[k] = __shfl_sync(0xffffffffu, rd[k], 0);
+    } else if (live) {
+      ray = source_ray(p.g, p.src, r);
+    }
+    if (live) {
+      c[0] = ray.tbar;
+      sample_coords(p.g, ray, j, p.S, c[1], c[2], c[3]);
+      if (j == 0 && half == 0) {
+        if (p.ray_l) p.ray_l[r] = (float)ray.l;
+        if (p.ray_p) p.ray_p[r] = p.proj ? p.proj[p.src.idx[r]] : 0.0f;
+      }
+    }
+  } else if (live) {
+    float len;
+    source_coords(p.g, p.src, smp, 0, 1, c, &len);
+    if (half == 0 && p.ray_l) p.ray_l[smp] = 1.0f;
+  }
+  float hi[4], lo[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    hi[k] = (float)c[k];
+    lo[k] = (float)(c[k] - (double)hi[k]);
+  }
+  for (int jc = half; jc < p.k0 / 64; jc += 2) {
+    uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+    for (int c16 = 0; c16 < 8; ++c16) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = 64 * jc + 8 * c16 + 2 * e;  // feature pair (col, col + 1)
+        float a = 0.0f, b = 0.0f;
+        if (live && col < 4) {
+          a = hi[col];
+          b = hi[col + 1];
+        } else if (live && col < p.d_in) {
+          const int idx = (col - 4) >> 1, k = idx / p.F, l = idx - k * p.F;
+          const float scale = (float)(1 << l);
+          const float x = hi[k] * scale;
+          const float y = (x - 2.0f * rintf(0.5f * x)) + lo[k] * scale;
+          sincospif(y, &a, &b);
+        }
+        w[e] = pack2(a, b);
+      }
+      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  fence_async_smem();
+  __syncwarp();
+  if (lane == 0 && p.store_h && tile * 128 + q * 32 < p.ns) {
+    for (int jc = half; jc < p.k0 / 64; jc += 2)
+      tma_store_2d(&maps.e, A + (size_t)jc * kChunkBytes + q * 32 * 128, 64 * jc,
+                   (int)(tile * 128 + q * 32));
+    bulk_commit();
+  }
+}
+
+// After layer L of one tile: bias + ReLU, BF16 back into the tile buffer,
+// TMA store of h_L, and on the last layer the output dot product.
+__device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
+                               int slot, uint32_t tcol, int L, long long tile, int q, int half,
+                               int lane, uint32_t dot_phase) {
+  const int r_in = q * 32 + lane;
+  const long long row = tile * 128 + r_in;
+  const bool live = row < p.ns;
+  const bool last = L == p.H - 1;
+  const uint32_t trow = tcol + ((uint32_t)(q * 32) << 16);
+  const float *bias = p.bias[L];
+  uint8_t *A = s.A[slot];
+  float dot = 0.0f;
+  for (int jc = half; jc < p.W / 64; jc += 2) {
+    float v[64];
+    tmem_ld32(trow + 64 * jc, *reinterpret_cast<float(*)[32]>(v));
+    tmem_ld32(trow + 64 * jc + 32, *reinterpret_cast<float(*)[32]>(v + 32));
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+      v[i] = fmaxf(v[i] + bias[64 * jc + i], 0.0f);
+      if (last) dot = fmaf(v[i], p.w_out[64 * jc + i], dot);
+    }
+    uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+#pragma unroll
+    for (int c16 = 0; c16 < 8; ++c16)
+      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) =
+          make_uint4(pack2(v[8 * c16], v[8 * c16 + 1]), pack2(v[8 * c16 + 2], v[8 * c16 + 3]),
+                     pack2(v[8 * c16 + 4], v[8 * c16 + 5]), pack2(v[8 * c16 + 6], v[8 * c16 + 7]));
+  }
+  fence_async_smem();
+  __syncwarp();
+  if (lane == 0 && p.store_h && tile * 128 + q * 32 < p.ns) {
+    for (int jc = half; jc < p.W / 64; jc += 2)
+      tma_store_2d(&maps.h[L], A + (size_t)jc * kChunkBytes + q * 32 * 128, 64 * jc,
+                   (int)(tile * 128 + q * 32));
+    bulk_commit();
+  }
+  if (last) {
+    float *db = s.dot + slot * 128;
+    if (half == 1) {
+      db[r_in] = dot;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s.dotbar[slot]);
+    } else {
+      if (!warp_wait(&s.dotbar[slot], dot_phase & 1, p.err, 15)) return false;
+      if (live) p.z_out[row] = dot + db[r_in] + p.b_out[0];
+    }
+  }
+  return true;
+}
+
+__device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
+                               uint32_t tbase) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int q = warp & 3, half = (warp - 2) / 4;
+  const int np = n_pairs(p);
+  uint32_t waits[2] = {0, 0}, dots[2] = {0, 0};
+  auto wait_stores = [&]() {
+    if (lane == 0) bulk_wait_read();  // earlier stores of this warp have read the buffer
+    __syncwarp();
+  };
+  if (np == 0) return;
+  for (int slot = 0; slot < 2; ++slot) {
+    encode_tile(maps, p, s.A[slot], tile_of(p, 0, slot), q, half, lane);
+    if (lane == 0) mbar_arrive(&s.aready[slot]);
+  }
+  for (int pr = 0; pr < np; ++pr)
+    for (int L = 0; L < p.H; ++L)
+      for (int slot = 0; slot < 2; ++slot) {
+        if (!warp_wait(&s.tfull[slot], waits[slot]++ & 1, p.err, 17)) return;
+        tc_fence_after();
+        wait_stores();
+        const long long tile = tile_of(p, pr, slot);
+        const bool last = L == p.H - 1;
+        if (!epilogue_layer(maps, p, s, slot, tbase + (uint32_t)(slot * p.W), L, tile, q, half,
+                            lane, last ? dots[slot]++ : 0))
+          return;
+        tc_fence_before();
+        if (last) {
+          if (pr + 1 == np) continue;
+          wait_stores();
+          encode_tile(maps, p, s.A[slot], tile_of(p, pr + 1, slot), q, half, lane);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s.aready[slot]);
+      }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_fwd_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainArgs p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  Smem s = carve(base, p);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(2 * p.W)) cols <<= 1;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < p.stages; ++i) {
+      mbar_init(&s.full[i], 1);
+      mbar_init(&s.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&s.aready[i], kEpiWarps);
+      mbar_init(&s.tfull[i], 1);
+      mbar_init(&s.dotbar[i], kEpiWarps / 2);
+    }
+    mbar_init(s.drain, 1);
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(s.tslot, cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *s.tslot;
+  if (warp == 0) {
+    if (lane == 0) producer(maps, p, s);
+  } else if (warp == 1) {
+    if (lane == 0) mma_issuer(p, s, tbase);
+  } else {
+    epilogue_warps(maps, p, s, tbase);
+    if (lane == 0) bulk_wait_all();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, cols);
+  }
+}
+
+}  // namespace
+
+size_t chain_smem_bytes(int W, int k0, int stages) {
+  return 2 * (size_t)a_chunks(W, k0) * kChunkBytes + (size_t)stages * W * 128 +
+         2 * 128 * sizeof(float) + 256 /*barriers*/ + 1024 /*alignment*/;
+}
+
+int chain_stages(int W, int k0) {
+  for (int st = 4; st >= 2; --st)
+    if (chain_smem_bytes(W, k0, st) <= (size_t)kSmemLimit) return st;
+  return 0;
+}
+
+int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
+  size_t smem = chain_smem_bytes(a.W, a.k0, a.stages);
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  int grid = a.m_tiles < num_sms ? a.m_tiles : num_sms;
+  k_fwd_chain<<<grid, kThreads, smem, st>>>(maps, a);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace dinr

@@ -183,7 +183,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
     uint4 hcur[4], hnext[4];
     if (p.epi == kTcDx && live && half < n_chunks)
       load_h32(p.hprev + (long long)row * p.ldh + half * 32, hcur);
-    if (!mbar_wait(&s.tfull[ab], ar & 1, p.err, 5)) return;
+    if (!warp_wait(&s.tfull[ab], ar & 1, p.err, 5)) return;
     tc_fence_after();
     const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)acc_stride(p);
     float dot = 0.0f;
@@ -249,7 +249,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&s.dotbar[ab]);
       } else {
-        if (!mbar_wait(&s.dotbar[ab], ar & 1, p.err, 7)) return;
+        if (!warp_wait(&s.dotbar[ab], ar & 1, p.err, 7)) return;
         if (live) p.z_out[row] = dot + db[r_in] + p.b_out[0];
       }
     }

@@ -7,8 +7,10 @@
 // all-ones MMA in the same kernel) and the input-gradient GEMM with the ReLU
 // mask fused. Master weights, gradients, segment sums and loss stay FP32.
 #include "tc.cuh"
+#include "tc_chain.cuh"
 #include "tc_gemm.cuh"
 
+#include <cstring>
 #include <vector>
 
 using namespace dinr;
@@ -144,6 +146,62 @@ dinr_status forward(dinr_ctx *c, long long ns) {
                          2.0 * ns * (acols + c->W), a, A, ns, acols, t->Wb[L], c->W, t->kpad[L]);
     if (s != DINR_OK) return s;
   }
+  return DINR_OK;
+}
+
+int chain_k0(const dinr_ctx *c) { return (c->d_in + 63) / 64 * 64; }
+
+bool chain_ok(const dinr_ctx *c) {
+  return c->W % 64 == 0 && c->W <= 256 && c->H <= kChainMaxLayers && chain_k0(c) <= 256 &&
+         chain_stages(c->W, chain_k0(c)) >= 2;
+}
+
+// The fused forward chain over a pass: rays of `src` (or points), encoding
+// in shared memory, all hidden layers, z_out; with store_h it also writes E
+// and every h_L for the backward.
+dinr_status chain(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S, bool store_h,
+                  const float *proj) {
+  TcState *t = S_(c);
+  const long long ns = n_rays * S;
+  ChainMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  bool ok = true;
+  for (int L = 0; L < c->H; ++L) {
+    ok = ok && make_tmap_bf16(&maps.w[L], t->Wb[L], c->W, t->kpad[L], t->kpad[L], c->W);
+    ok = ok && make_tmap_bf16(&maps.h[L], hid(c, L, ns), ns, c->W, c->W, 32);
+  }
+  ok = ok && make_tmap_bf16(&maps.e, t->E, ns, c->ldE, c->ldE, 32);
+  if (!ok) return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "tensor map encoding failed (chain)");
+  ChainArgs a{};
+  a.g = c->geo;
+  a.src = src;
+  a.n_rays = n_rays;
+  a.S = S;
+  a.F = c->F;
+  a.d_in = c->d_in;
+  a.k0 = chain_k0(c);
+  a.W = c->W;
+  a.H = c->H;
+  a.ns = ns;
+  a.m_tiles = (int)((ns + 127) / 128);
+  a.stages = chain_stages(c->W, a.k0);
+  a.store_h = store_h ? 1 : 0;
+  for (int L = 0; L < c->H; ++L) a.bias[L] = c->d_params + c->offb[L];
+  a.w_out = c->d_params + c->offW[c->H];
+  a.b_out = c->d_params + c->offb[c->H];
+  a.z_out = t->zout;
+  a.ray_l = t->ray_l;
+  a.ray_p = proj ? t->ray_p : nullptr;
+  a.proj = proj;
+  a.err = t->err;
+  double pw = (double)c->W * c->d_in + (double)(c->H - 1) * c->W * c->W + c->W;
+  ProfScope ps(c, "tc_fwd_chain", 2.0 * ns * pw,
+               store_h ? 2.0 * ns * (c->ldE + (double)c->H * c->W) : 4.0 * ns);
+  int e = launch_fwd_chain(maps, a, t->num_sms, c->st);
+  ++c->launches;
+  if (e != 0)
+    return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "chain launch: %s",
+                                  cudaGetErrorString((cudaError_t)e));
   return DINR_OK;
 }
 
@@ -316,13 +374,18 @@ dinr_status tc_loss_grad(dinr_ctx *c, int n) {
     SourceArgs src{};
     src.kind = kSrcTrainRays;
     src.idx = c->d_idx + r0;
-    {
-      ProfScope ps(c, "encode", 0.0, 2.0 * ns * c->ldE);
-      launch_encode_bf16(c->geo, src, nr, c->S, c->F, c->ldE, t->E, t->ray_l, c->d_proj,
-                         t->ray_p, c->st);
-      CKL();
+    dinr_status s;
+    if (chain_ok(c)) {
+      s = chain(c, src, nr, c->S, true, c->d_proj);
+    } else {
+      {
+        ProfScope ps(c, "encode", 0.0, 2.0 * ns * c->ldE);
+        launch_encode_bf16(c->geo, src, nr, c->S, c->F, c->ldE, t->E, t->ray_l, c->d_proj,
+                           t->ray_p, c->st);
+        CKL();
+      }
+      s = forward(c, ns);
     }
-    dinr_status s = forward(c, ns);
     if (s != DINR_OK) return s;
     launch_segsum(t->zout, c->out_act, nr, c->S, c->mu0, t->ray_l, t->ray_p, inv_B, true,
                   t->pbar, t->sq, t->dz, c->st);
@@ -348,10 +411,15 @@ static dinr_status tc_forward(dinr_ctx *c, const SourceArgs &src0, long long n_r
     else
       src.first = src0.first + r0;
     long long ns = nr * S;
-    launch_encode_bf16(c->geo, src, nr, S, c->F, c->ldE, t->E, t->ray_l, nullptr, nullptr,
-                       c->st);
-    CKL();
-    dinr_status s = forward(c, ns);
+    dinr_status s;
+    if (chain_ok(c)) {
+      s = chain(c, src, nr, S, false, nullptr);
+    } else {
+      launch_encode_bf16(c->geo, src, nr, S, c->F, c->ldE, t->E, t->ray_l, nullptr, nullptr,
+                         c->st);
+      CKL();
+      s = forward(c, ns);
+    }
     if (s != DINR_OK) return s;
     launch_segsum(t->zout, c->out_act, nr, S, c->mu0, t->ray_l, nullptr, 1.0f, false, out + r0,
                   nullptr, nullptr, c->st);
