@@ -140,32 +140,48 @@ __device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
 }
 
 // Layer-0 input of one tile: the Fourier features of its 128 samples, in
-// the K-chunks this warp owns (chunks half, half + 2, ...).
+// the K-chunks this warp owns (chunks half, half + 2, ...). F is a template
+// parameter so that every feature lands in a register by static index.
+// Octave features use exact sincospif at octaves 0, 4, 8, ... and angle
+// doubling in between (error about 1e-6, far below BF16 resolution).
+template <int F>
 __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *A,
                             long long tile, int q, int half, int lane) {
+  constexpr int kDin = 4 + 8 * F;
+  constexpr int kChunks = (kDin + 63) / 64;
   const int r_in = q * 32 + lane;
   const long long smp = tile * 128 + r_in;
   const bool live = smp < p.ns;
   const bool ray_src = p.src.kind == kSrcTrainRays || p.src.kind == kSrcVirtualView;
   double c[4] = {0.0, 0.0, 0.0, 0.0};
   if (ray_src) {
-    long long r = (live ? smp : 0) / p.S;
-    int j = (int)((live ? smp : 0) - r * p.S);
+    const long long s0 = live ? smp : 0;
+    const long long r = s0 / p.S;
+    const int j = (int)(s0 - r * p.S);
     Ray ray;
+    double step;
     const long long warp0 = tile * 128 + q * 32;
     if (p.S % 32 == 0) {
       // the warp's 32 consecutive samples lie on one ray: set it up once
-      if (lane == 0 && warp0 < p.ns) ray = source_ray(p.g, p.src, warp0 / p.S);
+      if (lane == 0 && warp0 < p.ns) {
+        ray = source_ray(p.g, p.src, warp0 / p.S);
+        step = ray.l / p.S;
+      }
       double *rd = reinterpret_cast<double *>(&ray);
 #pragma unroll
       for (int k = 0; k < (int)(sizeof(Ray) / sizeof(double)); ++k)
         rd[k] = __shfl_sync(0xffffffffu, rd[k], 0);
+      step = __shfl_sync(0xffffffffu, step, 0);
     } else if (live) {
       ray = source_ray(p.g, p.src, r);
+      step = ray.l / p.S;
     }
     if (live) {
+      const double sj = ray.s0 + (j + 0.5) * step;
       c[0] = ray.tbar;
-      sample_coords(p.g, ray, j, p.S, c[1], c[2], c[3]);
+      c[1] = (ray.oz + sj * ray.dz) * p.g.zs + p.g.zb;
+      c[2] = (ray.oy + sj * ray.dy) * p.g.inv_R;
+      c[3] = (ray.ox + sj * ray.dx) * p.g.inv_R;
       if (j == 0 && half == 0) {
         if (p.ray_l) p.ray_l[r] = (float)ray.l;
         if (p.ray_p) p.ray_p[r] = p.proj ? p.proj[p.src.idx[r]] : 0.0f;
@@ -176,39 +192,55 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
     source_coords(p.g, p.src, smp, 0, 1, c, &len);
     if (half == 0 && p.ray_l) p.ray_l[smp] = 1.0f;
   }
-  float hi[4], lo[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    hi[k] = (float)c[k];
-    lo[k] = (float)(c[k] - (double)hi[k]);
-  }
-  for (int jc = half; jc < p.k0 / 64; jc += 2) {
-    uint8_t *chunk = A + (size_t)jc * kChunkBytes;
-    for (int c16 = 0; c16 < 8; ++c16) {
-      uint32_t w[4];
+  for (int jc = 0; jc < kChunks; ++jc) {
+    if ((jc & 1) != half) continue;
+    uint32_t w[32];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int col = 64 * jc + 8 * c16 + 2 * e;  // feature pair (col, col + 1)
-        float a = 0.0f, b = 0.0f;
-        if (live && col < 4) {
-          a = hi[col];
-          b = hi[col + 1];
-        } else if (live && col < p.d_in) {
-          const int idx = (col - 4) >> 1, k = idx / p.F, l = idx - k * p.F;
-          const float scale = (float)(1 << l);
-          const float x = hi[k] * scale;
-          const float y = (x - 2.0f * rintf(0.5f * x)) + lo[k] * scale;
-          sincospif(y, &a, &b);
-        }
-        w[e] = pack2(a, b);
-      }
-      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
+    for (int i = 0; i < 32; ++i) w[i] = 0u;
+    if (jc == 0) {
+      w[0] = pack2((float)c[0], (float)c[1]);
+      w[1] = pack2((float)c[2], (float)c[3]);
     }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      constexpr int dummy = 0;
+      (void)dummy;
+      const int lo_col = 4 + 2 * F * k;
+      if (lo_col + 2 * F <= 64 * jc || lo_col >= 64 * (jc + 1)) continue;
+      const float hi = (float)c[k];
+      const float lo = (float)(c[k] - (double)hi);
+      float sp = 0.0f, cp = 1.0f, scale = 1.0f;
+#pragma unroll
+      for (int l = 0; l < F; ++l) {
+        if ((l & 3) == 0) {
+          const float x = hi * scale;
+          const float y = (x - 2.0f * rintf(0.5f * x)) + lo * scale;
+          sincospif(y, &sp, &cp);
+        } else {
+          const float s2 = 2.0f * sp * cp;
+          cp = (cp - sp) * (cp + sp);
+          sp = s2;
+        }
+        scale *= 2.0f;
+        const int col = lo_col + 2 * l;
+        if (col >= 64 * jc && col < 64 * (jc + 1)) w[(col - 64 * jc) / 2] = pack2(sp, cp);
+      }
+    }
+    if (!live) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) w[i] = 0u;
+    }
+    uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+#pragma unroll
+    for (int c16 = 0; c16 < 8; ++c16)
+      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) =
+          make_uint4(w[4 * c16], w[4 * c16 + 1], w[4 * c16 + 2], w[4 * c16 + 3]);
   }
   fence_async_smem();
   __syncwarp();
   if (lane == 0 && p.store_h && tile * 128 + q * 32 < p.ns) {
-    for (int jc = half; jc < p.k0 / 64; jc += 2)
+    for (int jc = half; jc < kChunks; jc += 2)
       tma_store_2d(&maps.e, A + (size_t)jc * kChunkBytes + q * 32 * 128, 64 * jc,
                    (int)(tile * 128 + q * 32));
     bulk_commit();
@@ -232,10 +264,25 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
     float v[64];
     tmem_ld32(trow + 64 * jc, *reinterpret_cast<float(*)[32]>(v));
     tmem_ld32(trow + 64 * jc + 32, *reinterpret_cast<float(*)[32]>(v + 32));
+    const float4 *b4 = reinterpret_cast<const float4 *>(bias + 64 * jc);
 #pragma unroll
-    for (int i = 0; i < 64; ++i) {
-      v[i] = fmaxf(v[i] + bias[64 * jc + i], 0.0f);
-      if (last) dot = fmaf(v[i], p.w_out[64 * jc + i], dot);
+    for (int i4 = 0; i4 < 16; ++i4) {
+      const float4 b = __ldg(b4 + i4);
+      v[4 * i4] = fmaxf(v[4 * i4] + b.x, 0.0f);
+      v[4 * i4 + 1] = fmaxf(v[4 * i4 + 1] + b.y, 0.0f);
+      v[4 * i4 + 2] = fmaxf(v[4 * i4 + 2] + b.z, 0.0f);
+      v[4 * i4 + 3] = fmaxf(v[4 * i4 + 3] + b.w, 0.0f);
+    }
+    if (last) {
+      const float4 *o4 = reinterpret_cast<const float4 *>(p.w_out + 64 * jc);
+#pragma unroll
+      for (int i4 = 0; i4 < 16; ++i4) {
+        const float4 o = __ldg(o4 + i4);
+        dot = fmaf(v[4 * i4], o.x, dot);
+        dot = fmaf(v[4 * i4 + 1], o.y, dot);
+        dot = fmaf(v[4 * i4 + 2], o.z, dot);
+        dot = fmaf(v[4 * i4 + 3], o.w, dot);
+      }
     }
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
 #pragma unroll
@@ -266,6 +313,7 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
   return true;
 }
 
+template <int F>
 __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
                                uint32_t tbase) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -278,7 +326,7 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
   };
   if (np == 0) return;
   for (int slot = 0; slot < 2; ++slot) {
-    encode_tile(maps, p, s.A[slot], tile_of(p, 0, slot), q, half, lane);
+    encode_tile<F>(maps, p, s.A[slot], tile_of(p, 0, slot), q, half, lane);
     if (lane == 0) mbar_arrive(&s.aready[slot]);
   }
   for (int pr = 0; pr < np; ++pr)
@@ -296,13 +344,14 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
         if (last) {
           if (pr + 1 == np) continue;
           wait_stores();
-          encode_tile(maps, p, s.A[slot], tile_of(p, pr + 1, slot), q, half, lane);
+          encode_tile<F>(maps, p, s.A[slot], tile_of(p, pr + 1, slot), q, half, lane);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s.aready[slot]);
       }
 }
 
+template <int F>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fwd_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainArgs p) {
   extern __shared__ uint8_t smem_raw[];
@@ -335,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) mma_issuer(p, s, tbase);
   } else {
-    epilogue_warps(maps, p, s, tbase);
+    epilogue_warps<F>(maps, p, s, tbase);
     if (lane == 0) bulk_wait_all();
   }
   tc_fence_before();
@@ -359,14 +408,28 @@ int chain_stages(int W, int k0) {
   return 0;
 }
 
-int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
+bool chain_supports_freq(int F) { return F == 6 || F == 8 || F == 10 || F == 12 || F == 16; }
+
+template <int F>
+static int launch_f(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
   size_t smem = chain_smem_bytes(a.W, a.k0, a.stages);
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_chain<F>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   int grid = a.m_tiles < num_sms ? a.m_tiles : num_sms;
-  k_fwd_chain<<<grid, kThreads, smem, st>>>(maps, a);
+  k_fwd_chain<F><<<grid, kThreads, smem, st>>>(maps, a);
   return (int)cudaGetLastError();
+}
+
+int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
+  switch (a.F) {
+    case 6: return launch_f<6>(maps, a, num_sms, st);
+    case 8: return launch_f<8>(maps, a, num_sms, st);
+    case 10: return launch_f<10>(maps, a, num_sms, st);
+    case 12: return launch_f<12>(maps, a, num_sms, st);
+    case 16: return launch_f<16>(maps, a, num_sms, st);
+    default: return (int)cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace dinr

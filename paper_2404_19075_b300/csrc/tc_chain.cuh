@@ -39,6 +39,7 @@ struct ChainArgs {
 // Shared memory the chain needs for a width, layer-0 K and stage count.
 size_t chain_smem_bytes(int W, int k0, int stages);
 int chain_stages(int W, int k0);
+bool chain_supports_freq(int F);
 int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st);
 
 }  // namespace dinr

@@ -152,8 +152,13 @@ dinr_status forward(dinr_ctx *c, long long ns) {
 int chain_k0(const dinr_ctx *c) { return (c->d_in + 63) / 64 * 64; }
 
 bool chain_ok(const dinr_ctx *c) {
-  return c->W % 64 == 0 && c->W <= 256 && c->H <= kChainMaxLayers && chain_k0(c) <= 256 &&
-         chain_stages(c->W, chain_k0(c)) >= 2;
+  if (!(c->W % 64 == 0 && c->W <= 256 && c->H <= kChainMaxLayers && chain_k0(c) <= 256 &&
+        chain_supports_freq(c->F) && chain_stages(c->W, chain_k0(c)) >= 2))
+    return false;
+  // biases and output weights are read as float4
+  for (int L = 0; L <= c->H; ++L)
+    if (c->offb[L] % 4 != 0) return false;
+  return c->offW[c->H] % 4 == 0;
 }
 
 // The fused forward chain over a pass: rays of `src` (or points), encoding
