@@ -1,4 +1,4 @@
-// Fused forward chain (see tc_chain.cuh).
+// Fused forward and backward chains (see tc_chain.cuh).
 //
 // One persistent CTA per SM, 320 threads:
 //   warp 0      one thread streams the weight K-chunks of every layer by TMA
@@ -76,23 +76,34 @@ __device__ __forceinline__ int n_pairs(const ChainArgs &p) {
   return (nt + 1) / 2;
 }
 
-__device__ __forceinline__ int layer_k(const ChainArgs &p, int L) { return L == 0 ? p.k0 : p.W; }
+// MMA steps of a tile: forward layers L = 0..H-1 (K = k0 for L = 0, else W);
+// backward input gradients through layers L = H-1..1 (K = W).
+template <bool kBwd>
+__device__ __forceinline__ int n_steps(const ChainArgs &p) { return kBwd ? p.H - 1 : p.H; }
+template <bool kBwd>
+__device__ __forceinline__ int step_layer(const ChainArgs &p, int i) { return kBwd ? p.H - 1 - i : i; }
+template <bool kBwd>
+__device__ __forceinline__ int step_k(const ChainArgs &p, int i) {
+  return (!kBwd && i == 0) ? p.k0 : p.W;
+}
 
 // ---------------------------------------------------------------- roles
 
+template <bool kBwd>
 __device__ void producer(const ChainMaps &maps, const ChainArgs &p, const Smem &s) {
-  for (int L = 0; L < p.H; ++L) prefetch_tmap(&maps.w[L]);
+  for (int i = 0; i < n_steps<kBwd>(p); ++i) prefetch_tmap(&maps.w[step_layer<kBwd>(p, i)]);
   const uint32_t S = p.stages, tx = (uint32_t)p.W * 128;
   uint32_t it = 0;
   const int np = n_pairs(p);
   for (int pr = 0; pr < np; ++pr)
-    for (int L = 0; L < p.H; ++L)
+    for (int i = 0; i < n_steps<kBwd>(p); ++i)
       for (int slot = 0; slot < 2; ++slot)
-        for (int kc = 0; kc < layer_k(p, L) / 64; ++kc, ++it) {
+        for (int kc = 0; kc < step_k<kBwd>(p, i) / 64; ++kc, ++it) {
           uint32_t st = it % S, rd = it / S;
           if (!mbar_wait(&s.empty[st], (rd & 1) ^ 1, p.err, 11)) goto drain;
           mbar_expect_tx(&s.full[st], tx);
-          tma_load_2d(&maps.w[L], &s.full[st], s.ring + (size_t)st * p.W * 128, 64 * kc, 0);
+          tma_load_2d(&maps.w[step_layer<kBwd>(p, i)], &s.full[st],
+                      s.ring + (size_t)st * p.W * 128, 64 * kc, 0);
         }
 drain:
   uint32_t n = it < S ? it : S;
@@ -100,6 +111,7 @@ drain:
     if (!mbar_wait(&s.full[q % S], (q / S) & 1, p.err, 16)) break;
 }
 
+template <bool kBwd>
 __device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
   const uint32_t S = p.stages;
   const uint32_t idesc = idesc_bf16(128, p.W, false, false);
@@ -107,7 +119,7 @@ __device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
   const int np = n_pairs(p);
   bool ok = true;
   for (int pr = 0; pr < np && ok; ++pr)
-    for (int L = 0; L < p.H && ok; ++L)
+    for (int i = 0; i < n_steps<kBwd>(p) && ok; ++i)
       for (int slot = 0; slot < 2 && ok; ++slot) {
         if (!mbar_wait(&s.aready[slot], waits[slot]++ & 1, p.err, 12)) {
           ok = false;
@@ -116,7 +128,7 @@ __device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
         tc_fence_after();
         const uint32_t d = tbase + (uint32_t)(slot * p.W);
         const uint32_t a0 = smem_u32(s.A[slot]);
-        const int nk = layer_k(p, L) / 64;
+        const int nk = step_k<kBwd>(p, i) / 64;
         for (int kc = 0; kc < nk; ++kc, ++it) {
           uint32_t st = it % S, rd = it / S;
           if (!mbar_wait(&s.full[st], rd & 1, p.err, 13)) {
@@ -139,6 +151,24 @@ __device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
   mbar_wait(s.drain, 0, p.err, 14);
 }
 
+// Per-ray setup in FP64 (Sec. III decode and rotation, FOV chord, App. A
+// midpoints, App. B normalisation), handed to FP32: normalised time, the
+// normalised position of sample 0, the normalised step between samples and
+// the chord length.
+__device__ __forceinline__ void ray_params(const ChainArgs &p, long long r, float (&pr)[8]) {
+  const Ray ray = source_ray(p.g, p.src, r);
+  const double step = ray.l / p.S;
+  const double s = ray.s0 + 0.5 * step;
+  pr[0] = (float)ray.tbar;
+  pr[1] = (float)((ray.oz + s * ray.dz) * p.g.zs + p.g.zb);
+  pr[2] = (float)((ray.oy + s * ray.dy) * p.g.inv_R);
+  pr[3] = (float)((ray.ox + s * ray.dx) * p.g.inv_R);
+  pr[4] = (float)(step * ray.dz * p.g.zs);
+  pr[5] = (float)(step * ray.dy * p.g.inv_R);
+  pr[6] = (float)(step * ray.dx * p.g.inv_R);
+  pr[7] = (float)ray.l;
+}
+
 // Layer-0 input of one tile: the Fourier features of its 128 samples, in
 // the K-chunks this warp owns (chunks half, half + 2, ...). F is a template
 // parameter so that every feature lands in a register by static index.
@@ -153,43 +183,42 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
   const long long smp = tile * 128 + r_in;
   const bool live = smp < p.ns;
   const bool ray_src = p.src.kind == kSrcTrainRays || p.src.kind == kSrcVirtualView;
-  double c[4] = {0.0, 0.0, 0.0, 0.0};
+  // Normalised (t, z, y, x) in FP32. A ray is set up once in FP64 (chord,
+  // normalised start point of its first sample and normalised step); its
+  // samples are then start + j * step in FP32, whose rounding (about 1e-7)
+  // moves the phase of the highest octave by under 1e-3 rad, below BF16
+  // resolution of the features.
+  float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (ray_src) {
     const long long s0 = live ? smp : 0;
     const long long r = s0 / p.S;
     const int j = (int)(s0 - r * p.S);
-    Ray ray;
-    double step;
+    float pr[8];  // tbar, start (z, y, x), step (z, y, x), chord length
     const long long warp0 = tile * 128 + q * 32;
     if (p.S % 32 == 0) {
       // the warp's 32 consecutive samples lie on one ray: set it up once
-      if (lane == 0 && warp0 < p.ns) {
-        ray = source_ray(p.g, p.src, warp0 / p.S);
-        step = ray.l / p.S;
-      }
-      double *rd = reinterpret_cast<double *>(&ray);
+      if (lane == 0 && warp0 < p.ns) ray_params(p, warp0 / p.S, pr);
 #pragma unroll
-      for (int k = 0; k < (int)(sizeof(Ray) / sizeof(double)); ++k)
-        rd[k] = __shfl_sync(0xffffffffu, rd[k], 0);
-      step = __shfl_sync(0xffffffffu, step, 0);
+      for (int k = 0; k < 8; ++k) pr[k] = __shfl_sync(0xffffffffu, pr[k], 0);
     } else if (live) {
-      ray = source_ray(p.g, p.src, r);
-      step = ray.l / p.S;
+      ray_params(p, r, pr);
     }
     if (live) {
-      const double sj = ray.s0 + (j + 0.5) * step;
-      c[0] = ray.tbar;
-      c[1] = (ray.oz + sj * ray.dz) * p.g.zs + p.g.zb;
-      c[2] = (ray.oy + sj * ray.dy) * p.g.inv_R;
-      c[3] = (ray.ox + sj * ray.dx) * p.g.inv_R;
+      c[0] = pr[0];
+      c[1] = fmaf((float)j, pr[4], pr[1]);
+      c[2] = fmaf((float)j, pr[5], pr[2]);
+      c[3] = fmaf((float)j, pr[6], pr[3]);
       if (j == 0 && half == 0) {
-        if (p.ray_l) p.ray_l[r] = (float)ray.l;
+        if (p.ray_l) p.ray_l[r] = pr[7];
         if (p.ray_p) p.ray_p[r] = p.proj ? p.proj[p.src.idx[r]] : 0.0f;
       }
     }
   } else if (live) {
+    double cd[4];
     float len;
-    source_coords(p.g, p.src, smp, 0, 1, c, &len);
+    source_coords(p.g, p.src, smp, 0, 1, cd, &len);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = (float)cd[k];
     if (half == 0 && p.ray_l) p.ray_l[smp] = 1.0f;
   }
 #pragma unroll
@@ -199,8 +228,8 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
 #pragma unroll
     for (int i = 0; i < 32; ++i) w[i] = 0u;
     if (jc == 0) {
-      w[0] = pack2((float)c[0], (float)c[1]);
-      w[1] = pack2((float)c[2], (float)c[3]);
+      w[0] = pack2(c[0], c[1]);
+      w[1] = pack2(c[2], c[3]);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -208,14 +237,13 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
       (void)dummy;
       const int lo_col = 4 + 2 * F * k;
       if (lo_col + 2 * F <= 64 * jc || lo_col >= 64 * (jc + 1)) continue;
-      const float hi = (float)c[k];
-      const float lo = (float)(c[k] - (double)hi);
+      const float hi = c[k];
       float sp = 0.0f, cp = 1.0f, scale = 1.0f;
 #pragma unroll
       for (int l = 0; l < F; ++l) {
         if ((l & 3) == 0) {
           const float x = hi * scale;
-          const float y = (x - 2.0f * rintf(0.5f * x)) + lo * scale;
+          const float y = x - 2.0f * rintf(0.5f * x);
           sincospif(y, &sp, &cp);
         } else {
           const float s2 = 2.0f * sp * cp;
@@ -313,47 +341,167 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
   return true;
 }
 
-template <int F>
+// ------------------------------------------------------ backward chain
+
+__device__ __forceinline__ void load_row64(const __nv_bfloat16 *p, uint4 (&h)[8]) {
+  const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) h[j] = q[j];
+}
+
+__device__ __forceinline__ float keep_if_pos(float x, uint32_t hbits) {
+  return (hbits != 0 && (hbits & 0x8000u) == 0) ? x : 0.0f;  // h > 0 in BF16
+}
+
+// Store this warp's chunks of the tile buffer through maps.h[L].
+__device__ __forceinline__ void store_chunks(const ChainMaps &maps, const ChainArgs &p,
+                                             uint8_t *A, int L, long long tile, int q, int half,
+                                             int lane) {
+  fence_async_smem();
+  __syncwarp();
+  if (lane == 0 && p.store_h && tile * 128 + q * 32 < p.ns) {
+    for (int jc = half; jc < p.W / 64; jc += 2)
+      tma_store_2d(&maps.h[L], A + (size_t)jc * kChunkBytes + q * 32 * 128, 64 * jc,
+                   (int)(tile * 128 + q * 32));
+    bulk_commit();
+  }
+}
+
+// delta_{H-1}[s][c] = dz[s] * w_out[c] * [h_{H-1}[s][c] > 0] into the tile buffer.
+__device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t *A,
+                             long long tile, int q, int half, int lane) {
+  const int r_in = q * 32 + lane;
+  const long long row = tile * 128 + r_in;
+  const bool live = row < p.ns;
+  const float dzr = live ? p.dz[row] : 0.0f;
+  const __nv_bfloat16 *h = p.hs[p.H - 1] + (live ? row : 0) * p.W;
+  for (int jc = half; jc < p.W / 64; jc += 2) {
+    uint4 hb[8];
+    if (live) load_row64(h + 64 * jc, hb);
+    const float4 *o4 = reinterpret_cast<const float4 *>(p.w_out + 64 * jc);
+    uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+#pragma unroll
+    for (int c16 = 0; c16 < 8; ++c16) {
+      const float4 oa = __ldg(o4 + 2 * c16), ob = __ldg(o4 + 2 * c16 + 1);
+      const float o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      if (live) {
+        const uint32_t hw[4] = {hb[c16].x, hb[c16].y, hb[c16].z, hb[c16].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          w[e] = pack2(keep_if_pos(dzr * o[2 * e], hw[e] & 0xFFFFu),
+                       keep_if_pos(dzr * o[2 * e + 1], hw[e] >> 16));
+      }
+      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  store_chunks(maps, p, A, p.H - 1, tile, q, half, lane);
+}
+
+// After the input-gradient GEMM through layer L: delta_{L-1} = acc * [h_{L-1} > 0].
+__device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Smem &s, int slot,
+                             uint32_t tcol, int L, long long tile, int q, int half, int lane,
+                             uint32_t tfull_phase) {
+  const int r_in = q * 32 + lane;
+  const long long row = tile * 128 + r_in;
+  const bool live = row < p.ns;
+  const __nv_bfloat16 *h = p.hs[L - 1] + (live ? row : 0) * p.W;
+  uint4 hb[8];
+  if (live && half < p.W / 64) load_row64(h + 64 * half, hb);  // before the wait
+  if (!warp_wait(&s.tfull[slot], tfull_phase & 1, p.err, 18)) return false;
+  tc_fence_after();
+  if (lane == 0) bulk_wait_read();
+  __syncwarp();
+  const uint32_t trow = tcol + ((uint32_t)(q * 32) << 16);
+  uint8_t *A = s.A[slot];
+  for (int jc = half; jc < p.W / 64; jc += 2) {
+    float v[64];
+    tmem_ld32(trow + 64 * jc, *reinterpret_cast<float(*)[32]>(v));
+    tmem_ld32(trow + 64 * jc + 32, *reinterpret_cast<float(*)[32]>(v + 32));
+    uint32_t hw[32];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      hw[4 * j] = hb[j].x;
+      hw[4 * j + 1] = hb[j].y;
+      hw[4 * j + 2] = hb[j].z;
+      hw[4 * j + 3] = hb[j].w;
+    }
+    if (live && jc + 2 < p.W / 64) load_row64(h + 64 * (jc + 2), hb);
+    uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+#pragma unroll
+    for (int c16 = 0; c16 < 8; ++c16) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = 8 * c16 + 2 * e;
+        const uint32_t hh = hw[i >> 1];
+        w[e] = live ? pack2(keep_if_pos(v[i], hh & 0xFFFFu), keep_if_pos(v[i + 1], hh >> 16))
+                    : 0u;
+      }
+      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  store_chunks(maps, p, A, L - 1, tile, q, half, lane);
+  return true;
+}
+
+// ------------------------------------------------------- epilogue warps
+
+template <int F, bool kBwd>
 __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
                                uint32_t tbase) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int q = warp & 3, half = (warp - 2) / 4;
   const int np = n_pairs(p);
+  const int ns = n_steps<kBwd>(p);
   uint32_t waits[2] = {0, 0}, dots[2] = {0, 0};
   auto wait_stores = [&]() {
     if (lane == 0) bulk_wait_read();  // earlier stores of this warp have read the buffer
     __syncwarp();
   };
+  auto start_tile = [&](int slot, long long tile) {
+    if (kBwd)
+      bwd_prologue(maps, p, s.A[slot], tile, q, half, lane);
+    else
+      encode_tile<F>(maps, p, s.A[slot], tile, q, half, lane);
+  };
   if (np == 0) return;
   for (int slot = 0; slot < 2; ++slot) {
-    encode_tile<F>(maps, p, s.A[slot], tile_of(p, 0, slot), q, half, lane);
+    start_tile(slot, tile_of(p, 0, slot));
     if (lane == 0) mbar_arrive(&s.aready[slot]);
   }
   for (int pr = 0; pr < np; ++pr)
-    for (int L = 0; L < p.H; ++L)
+    for (int i = 0; i < ns; ++i)
       for (int slot = 0; slot < 2; ++slot) {
-        if (!warp_wait(&s.tfull[slot], waits[slot]++ & 1, p.err, 17)) return;
-        tc_fence_after();
-        wait_stores();
         const long long tile = tile_of(p, pr, slot);
-        const bool last = L == p.H - 1;
-        if (!epilogue_layer(maps, p, s, slot, tbase + (uint32_t)(slot * p.W), L, tile, q, half,
-                            lane, last ? dots[slot]++ : 0))
-          return;
+        const bool last = i == ns - 1;
+        const uint32_t tcol = tbase + (uint32_t)(slot * p.W);
+        if (kBwd) {
+          if (!bwd_epilogue(maps, p, s, slot, tcol, step_layer<true>(p, i), tile, q, half, lane,
+                            waits[slot]++))
+            return;
+        } else {
+          if (!warp_wait(&s.tfull[slot], waits[slot]++ & 1, p.err, 17)) return;
+          tc_fence_after();
+          wait_stores();
+          if (!epilogue_layer(maps, p, s, slot, tcol, i, tile, q, half, lane,
+                              last ? dots[slot]++ : 0))
+            return;
+        }
         tc_fence_before();
         if (last) {
           if (pr + 1 == np) continue;
           wait_stores();
-          encode_tile<F>(maps, p, s.A[slot], tile_of(p, pr + 1, slot), q, half, lane);
+          start_tile(slot, tile_of(p, pr + 1, slot));
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s.aready[slot]);
       }
 }
 
-template <int F>
+template <int F, bool kBwd>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_fwd_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainArgs p) {
+    k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -380,11 +528,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tbase = *s.tslot;
   if (warp == 0) {
-    if (lane == 0) producer(maps, p, s);
+    if (lane == 0) producer<kBwd>(maps, p, s);
   } else if (warp == 1) {
-    if (lane == 0) mma_issuer(p, s, tbase);
+    if (lane == 0) mma_issuer<kBwd>(p, s, tbase);
   } else {
-    epilogue_warps<F>(maps, p, s, tbase);
+    epilogue_warps<F, kBwd>(maps, p, s, tbase);
     if (lane == 0) bulk_wait_all();
   }
   tc_fence_before();
@@ -410,26 +558,31 @@ int chain_stages(int W, int k0) {
 
 bool chain_supports_freq(int F) { return F == 6 || F == 8 || F == 10 || F == 12 || F == 16; }
 
-template <int F>
+template <int F, bool kBwd>
 static int launch_f(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
   size_t smem = chain_smem_bytes(a.W, a.k0, a.stages);
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_chain<F>,
+  cudaError_t e = cudaFuncSetAttribute(k_chain<F, kBwd>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   int grid = a.m_tiles < num_sms ? a.m_tiles : num_sms;
-  k_fwd_chain<F><<<grid, kThreads, smem, st>>>(maps, a);
+  k_chain<F, kBwd><<<grid, kThreads, smem, st>>>(maps, a);
   return (int)cudaGetLastError();
 }
 
 int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
   switch (a.F) {
-    case 6: return launch_f<6>(maps, a, num_sms, st);
-    case 8: return launch_f<8>(maps, a, num_sms, st);
-    case 10: return launch_f<10>(maps, a, num_sms, st);
-    case 12: return launch_f<12>(maps, a, num_sms, st);
-    case 16: return launch_f<16>(maps, a, num_sms, st);
+    case 6: return launch_f<6, false>(maps, a, num_sms, st);
+    case 8: return launch_f<8, false>(maps, a, num_sms, st);
+    case 10: return launch_f<10, false>(maps, a, num_sms, st);
+    case 12: return launch_f<12, false>(maps, a, num_sms, st);
+    case 16: return launch_f<16, false>(maps, a, num_sms, st);
     default: return (int)cudaErrorInvalidValue;
   }
+}
+
+int launch_bwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
+  if (a.H < 2) return (int)cudaErrorInvalidValue;
+  return launch_f<0, true>(maps, a, num_sms, st);
 }
 
 }  // namespace dinr

@@ -12,9 +12,11 @@ namespace dinr {
 constexpr int kChainMaxLayers = 8;
 
 struct ChainMaps {
-  CUtensorMap w[kChainMaxLayers];  // BF16 weights W_L [W][K_L], box {64, W}
-  CUtensorMap h[kChainMaxLayers];  // BF16 outputs h_L [samples][W], box {64, 32}
-  CUtensorMap e;                   // BF16 features E [samples][ldE], box {64, 32}
+  // forward: BF16 weights W_L [W][K_L]; backward: transposed W_L^T [W][W]; box {64, W}
+  CUtensorMap w[kChainMaxLayers];
+  // forward: outputs h_L; backward: deltas delta_L; [samples][W], box {64, 32}
+  CUtensorMap h[kChainMaxLayers];
+  CUtensorMap e;                   // forward: features E [samples][ldE], box {64, 32}
 };
 
 struct ChainArgs {
@@ -33,6 +35,9 @@ struct ChainArgs {
   float *z_out;                    // [ns]
   float *ray_l, *ray_p;            // [n_rays]
   const float *proj;               // measured stack (training rays) or null
+  // backward chain
+  const float *dz;                 // dL/dz_out per sample
+  const __nv_bfloat16 *hs[kChainMaxLayers];  // forward outputs h_L (ReLU masks)
   int *err;
 };
 
@@ -41,5 +46,9 @@ size_t chain_smem_bytes(int W, int k0, int stages);
 int chain_stages(int W, int k0);
 bool chain_supports_freq(int F);
 int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st);
+// Backward chain (H >= 2): delta_{H-1} = dz w_out [h_{H-1} > 0], then
+// delta_{L-1} = (delta_L W_L) [h_{L-1} > 0] for L = H-1..1, all on chip;
+// every delta_L is stored through maps.h[L].
+int launch_bwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st);
 
 }  // namespace dinr

@@ -37,6 +37,8 @@ struct TcState {
   std::vector<__nv_bfloat16 *> Wb, WbT;  // per hidden layer: [fan_out][kpad], [fan_in][W]
   std::vector<int> kpad;
   __nv_bfloat16 *E = nullptr, *H = nullptr, *D0 = nullptr, *D1 = nullptr;
+  __nv_bfloat16 *Dall = nullptr;  // [H][samples][W] deltas of every layer (chain path)
+  bool chain = false;
   float *zout = nullptr, *dz = nullptr, *ray_l = nullptr, *ray_p = nullptr, *pbar = nullptr,
         *sq = nullptr, *part = nullptr, *part_db = nullptr;
   long long part_floats = 0;
@@ -210,6 +212,40 @@ dinr_status chain(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S, b
   return DINR_OK;
 }
 
+// Backward chain over a pass: every delta_L into Dall.
+dinr_status bwd_chain(dinr_ctx *c, long long ns) {
+  TcState *t = S_(c);
+  ChainMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  bool ok = true;
+  for (int L = 0; L < c->H; ++L) {
+    if (L > 0) ok = ok && make_tmap_bf16(&maps.w[L], t->WbT[L], c->W, c->W, c->W, c->W);
+    ok = ok && make_tmap_bf16(&maps.h[L], t->Dall + (long long)L * ns * c->W, ns, c->W, c->W, 32);
+  }
+  if (!ok) return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "tensor map encoding failed (bwd)");
+  ChainArgs a{};
+  a.g = c->geo;
+  a.W = c->W;
+  a.H = c->H;
+  a.k0 = chain_k0(c);
+  a.ns = ns;
+  a.m_tiles = (int)((ns + 127) / 128);
+  a.stages = chain_stages(c->W, a.k0);
+  a.store_h = 1;
+  a.w_out = c->d_params + c->offW[c->H];
+  a.dz = t->dz;
+  for (int L = 0; L < c->H; ++L) a.hs[L] = hid(c, L, ns);
+  a.err = t->err;
+  ProfScope ps(c, "tc_bwd_chain", 2.0 * ns * (double)(c->H - 1) * c->W * c->W,
+               2.0 * ns * c->W * (2.0 * c->H));
+  int e = launch_bwd_chain(maps, a, t->num_sms, c->st);
+  ++c->launches;
+  if (e != 0)
+    return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "backward chain launch: %s",
+                                  cudaGetErrorString((cudaError_t)e));
+  return DINR_OK;
+}
+
 dinr_status reduce_into(dinr_ctx *c, const float *part, int splits, long long C, long long off,
                         bool acc) {
   launch_reduce_partials(part, splits, C, c->d_grad + off, acc, c->st);
@@ -222,9 +258,11 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
   const int W = c->W;
   __nv_bfloat16 *hH = hid(c, c->H - 1, ns);
   // output layer: delta_H, grad w_out = sum dz h_H, grad b_out = sum dz
-  k_out_delta_bf16<<<ceil_div(ns * W, 256), 256, 0, c->st>>>(t->dz, c->d_params + c->offW[c->H],
-                                                             hH, W, ns, t->D0);
-  CKL();
+  if (!t->chain) {
+    k_out_delta_bf16<<<ceil_div(ns * W, 256), 256, 0, c->st>>>(
+        t->dz, c->d_params + c->offW[c->H], hH, W, ns, t->D0);
+    CKL();
+  }
   int cs = colsum_splits(ns);
   k_colsum_bf16<<<dim3(ceil_div(W, 256), cs), 256, 0, c->st>>>(hH, W, ns, t->dz, cs, t->part);
   CKL();
@@ -235,8 +273,14 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
   s = reduce_into(c, t->part, cs, 1, c->offb[c->H], acc);
   if (s != DINR_OK) return s;
 
-  __nv_bfloat16 *D = t->D0, *Dn = t->D1;
+  if (t->chain) {
+    s = bwd_chain(c, ns);
+    if (s != DINR_OK) return s;
+  }
+  __nv_bfloat16 *D = t->chain ? t->Dall + (long long)(c->H - 1) * ns * W : t->D0;
+  __nv_bfloat16 *Dn = t->D1;
   for (int L = c->H - 1; L >= 0; --L) {
+    if (t->chain) D = t->Dall + (long long)L * ns * W;
     const void *In = L == 0 ? (const void *)t->E : (const void *)hid(c, L - 1, ns);
     int in_cols = L == 0 ? c->ldE : W;
     int fan_in = c->fan_in[L];
@@ -263,7 +307,7 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
     if (s != DINR_OK) return s;
     s = reduce_into(c, t->part_db, a.splits, W, c->offb[L], acc);
     if (s != DINR_OK) return s;
-    if (L > 0) {
+    if (L > 0 && !t->chain) {
       TcGemmArgs b{};
       b.epi = kTcDx;
       b.M = (int)ns;
@@ -301,6 +345,8 @@ dinr_status check_err(dinr_ctx *c) {
 
 }  // namespace
 
+static bool chains_used(const dinr_ctx *c);
+
 bool tc_supported(const dinr_net *net) {
   // ReLU hidden layers; widths in [32, 256], multiples of 32 (one N tile,
   // whole 32-column TMEM loads); at most 16 octaves (<= 144 padded inputs).
@@ -309,8 +355,11 @@ bool tc_supported(const dinr_net *net) {
 }
 
 long long tc_bytes_per_sample(const dinr_ctx *c) {
-  return 2LL * (c->ldE + (long long)(c->H + 2) * c->W) + 8 + 16;
+  long long deltas = chains_used(c) ? c->H : 2;
+  return 2LL * (c->ldE + (long long)(c->H + deltas) * c->W) + 8 + 16;
 }
+
+static bool chains_used(const dinr_ctx *c) { return chain_ok(c) && c->H >= 2; }
 
 dinr_status tc_alloc(dinr_ctx *c) {
   TcState *t = new TcState();
@@ -341,9 +390,13 @@ dinr_status tc_alloc(dinr_ctx *c) {
   long long pf = (long long)kMaxSplits * c->W * maxN;
   long long pc = (long long)colsum_splits(ns) * c->W;
   t->part_floats = pf > pc ? pf : pc;
+  t->chain = chains_used(c);
+  if (t->chain)
+    ok = ok && grab((void **)&t->Dall, 2ull * ns * c->W * c->H);
+  else
+    ok = ok && grab((void **)&t->D0, 2ull * ns * c->W) && grab((void **)&t->D1, 2ull * ns * c->W);
   ok = ok && grab((void **)&t->E, 2ull * ns * c->ldE) &&
-       grab((void **)&t->H, 2ull * ns * c->W * c->H) && grab((void **)&t->D0, 2ull * ns * c->W) &&
-       grab((void **)&t->D1, 2ull * ns * c->W) && grab((void **)&t->zout, 4ull * ns) &&
+       grab((void **)&t->H, 2ull * ns * c->W * c->H) && grab((void **)&t->zout, 4ull * ns) &&
        grab((void **)&t->dz, 4ull * ns) && grab((void **)&t->ray_l, 4ull * ns) &&
        grab((void **)&t->ray_p, 4ull * ns) && grab((void **)&t->pbar, 4ull * ns) &&
        grab((void **)&t->sq, 4ull * ns) && grab((void **)&t->part, 4ull * t->part_floats) &&
