@@ -151,24 +151,6 @@ __device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
   mbar_wait(s.drain, 0, p.err, 14);
 }
 
-// Per-ray setup in FP64 (Sec. III decode and rotation, FOV chord, App. A
-// midpoints, App. B normalisation), handed to FP32: normalised time, the
-// normalised position of sample 0, the normalised step between samples and
-// the chord length.
-__device__ __forceinline__ void ray_params(const ChainArgs &p, long long r, float (&pr)[8]) {
-  const Ray ray = source_ray(p.g, p.src, r);
-  const double step = ray.l / p.S;
-  const double s = ray.s0 + 0.5 * step;
-  pr[0] = (float)ray.tbar;
-  pr[1] = (float)((ray.oz + s * ray.dz) * p.g.zs + p.g.zb);
-  pr[2] = (float)((ray.oy + s * ray.dy) * p.g.inv_R);
-  pr[3] = (float)((ray.ox + s * ray.dx) * p.g.inv_R);
-  pr[4] = (float)(step * ray.dz * p.g.zs);
-  pr[5] = (float)(step * ray.dy * p.g.inv_R);
-  pr[6] = (float)(step * ray.dx * p.g.inv_R);
-  pr[7] = (float)ray.l;
-}
-
 // Layer-0 input of one tile: the Fourier features of its 128 samples, in
 // the K-chunks this warp owns (chunks half, half + 2, ...). F is a template
 // parameter so that every feature lands in a register by static index.
@@ -193,25 +175,14 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
     const long long s0 = live ? smp : 0;
     const long long r = s0 / p.S;
     const int j = (int)(s0 - r * p.S);
-    float pr[8];  // tbar, start (z, y, x), step (z, y, x), chord length
-    const long long warp0 = tile * 128 + q * 32;
-    if (p.S % 32 == 0) {
-      // the warp's 32 consecutive samples lie on one ray: set it up once
-      if (lane == 0 && warp0 < p.ns) ray_params(p, warp0 / p.S, pr);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) pr[k] = __shfl_sync(0xffffffffu, pr[k], 0);
-    } else if (live) {
-      ray_params(p, r, pr);
-    }
     if (live) {
-      c[0] = pr[0];
-      c[1] = fmaf((float)j, pr[4], pr[1]);
-      c[2] = fmaf((float)j, pr[5], pr[2]);
-      c[3] = fmaf((float)j, pr[6], pr[3]);
-      if (j == 0 && half == 0) {
-        if (p.ray_l) p.ray_l[r] = pr[7];
-        if (p.ray_p) p.ray_p[r] = p.proj ? p.proj[p.src.idx[r]] : 0.0f;
-      }
+      // tbar, start (z, y, x), step (z, y, x), chord length
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r));
+      const float4 b = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r) + 1);
+      c[0] = a.x;
+      c[1] = fmaf((float)j, b.x, a.y);
+      c[2] = fmaf((float)j, b.y, a.z);
+      c[3] = fmaf((float)j, b.z, a.w);
     }
   } else if (live) {
     double cd[4];
@@ -313,11 +284,23 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
       }
     }
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+    uint32_t bits[2] = {0u, 0u};
 #pragma unroll
-    for (int c16 = 0; c16 < 8; ++c16)
-      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) =
-          make_uint4(pack2(v[8 * c16], v[8 * c16 + 1]), pack2(v[8 * c16 + 2], v[8 * c16 + 3]),
-                     pack2(v[8 * c16 + 4], v[8 * c16 + 5]), pack2(v[8 * c16 + 6], v[8 * c16 + 7]));
+    for (int c16 = 0; c16 < 8; ++c16) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        w[e] = pack2(v[8 * c16 + 2 * e], v[8 * c16 + 2 * e + 1]);
+        // ReLU bit of each stored BF16 value: nonzero (it is never negative)
+        const int b = 8 * c16 + 2 * e;
+        bits[b >> 5] |= ((w[e] & 0xFFFFu) ? 1u : 0u) << (b & 31);
+        bits[b >> 5] |= ((w[e] >> 16) ? 1u : 0u) << ((b + 1) & 31);
+      }
+      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (live && p.masks[L])
+      *reinterpret_cast<uint2 *>(p.masks[L] + row * (p.W / 32) + 2 * jc) =
+          make_uint2(bits[0], bits[1]);
   }
   fence_async_smem();
   __syncwarp();
@@ -343,15 +326,7 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
 
 // ------------------------------------------------------ backward chain
 
-__device__ __forceinline__ void load_row64(const __nv_bfloat16 *p, uint4 (&h)[8]) {
-  const uint4 *q = reinterpret_cast<const uint4 *>(p);
-#pragma unroll
-  for (int j = 0; j < 8; ++j) h[j] = q[j];
-}
 
-__device__ __forceinline__ float keep_if_pos(float x, uint32_t hbits) {
-  return (hbits != 0 && (hbits & 0x8000u) == 0) ? x : 0.0f;  // h > 0 in BF16
-}
 
 // Store this warp's chunks of the tile buffer through maps.h[L].
 __device__ __forceinline__ void store_chunks(const ChainMaps &maps, const ChainArgs &p,
@@ -374,24 +349,21 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
   const long long row = tile * 128 + r_in;
   const bool live = row < p.ns;
   const float dzr = live ? p.dz[row] : 0.0f;
-  const __nv_bfloat16 *h = p.hs[p.H - 1] + (live ? row : 0) * p.W;
+  const uint32_t *mrow = p.masks[p.H - 1] + (live ? row : 0) * (p.W / 32);
   for (int jc = half; jc < p.W / 64; jc += 2) {
-    uint4 hb[8];
-    if (live) load_row64(h + 64 * jc, hb);
+    const uint2 mb = live ? *reinterpret_cast<const uint2 *>(mrow + 2 * jc) : make_uint2(0u, 0u);
     const float4 *o4 = reinterpret_cast<const float4 *>(p.w_out + 64 * jc);
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
 #pragma unroll
     for (int c16 = 0; c16 < 8; ++c16) {
       const float4 oa = __ldg(o4 + 2 * c16), ob = __ldg(o4 + 2 * c16 + 1);
       const float o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
-      uint32_t w[4] = {0u, 0u, 0u, 0u};
-      if (live) {
-        const uint32_t hw[4] = {hb[c16].x, hb[c16].y, hb[c16].z, hb[c16].w};
+      const uint32_t m = (c16 < 4 ? mb.x : mb.y) >> ((8 * c16) & 31);
+      uint32_t w[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          w[e] = pack2(keep_if_pos(dzr * o[2 * e], hw[e] & 0xFFFFu),
-                       keep_if_pos(dzr * o[2 * e + 1], hw[e] >> 16));
-      }
+      for (int e = 0; e < 4; ++e)
+        w[e] = pack2((m >> (2 * e)) & 1u ? dzr * o[2 * e] : 0.0f,
+                     (m >> (2 * e + 1)) & 1u ? dzr * o[2 * e + 1] : 0.0f);
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
@@ -405,38 +377,31 @@ __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Sm
   const int r_in = q * 32 + lane;
   const long long row = tile * 128 + r_in;
   const bool live = row < p.ns;
-  const __nv_bfloat16 *h = p.hs[L - 1] + (live ? row : 0) * p.W;
-  uint4 hb[8];
-  if (live && half < p.W / 64) load_row64(h + 64 * half, hb);  // before the wait
+  const uint32_t *mrow = p.masks[L - 1] + (live ? row : 0) * (p.W / 32);
+  uint2 mb[2] = {make_uint2(0u, 0u), make_uint2(0u, 0u)};
+  if (live)  // before the wait: the ReLU bits of this warp's (at most two) chunks
+    for (int k = 0; k < 2 && half + 2 * k < p.W / 64; ++k)
+      mb[k] = *reinterpret_cast<const uint2 *>(mrow + 2 * (half + 2 * k));
   if (!warp_wait(&s.tfull[slot], tfull_phase & 1, p.err, 18)) return false;
   tc_fence_after();
   if (lane == 0) bulk_wait_read();
   __syncwarp();
   const uint32_t trow = tcol + ((uint32_t)(q * 32) << 16);
   uint8_t *A = s.A[slot];
-  for (int jc = half; jc < p.W / 64; jc += 2) {
+  for (int k = 0, jc = half; jc < p.W / 64; ++k, jc += 2) {
     float v[64];
     tmem_ld32(trow + 64 * jc, *reinterpret_cast<float(*)[32]>(v));
     tmem_ld32(trow + 64 * jc + 32, *reinterpret_cast<float(*)[32]>(v + 32));
-    uint32_t hw[32];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      hw[4 * j] = hb[j].x;
-      hw[4 * j + 1] = hb[j].y;
-      hw[4 * j + 2] = hb[j].z;
-      hw[4 * j + 3] = hb[j].w;
-    }
-    if (live && jc + 2 < p.W / 64) load_row64(h + 64 * (jc + 2), hb);
+    const uint2 m2 = k == 0 ? mb[0] : mb[1];
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
 #pragma unroll
     for (int c16 = 0; c16 < 8; ++c16) {
+      const uint32_t m = (c16 < 4 ? m2.x : m2.y) >> ((8 * c16) & 31);
       uint32_t w[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int i = 8 * c16 + 2 * e;
-        const uint32_t hh = hw[i >> 1];
-        w[e] = live ? pack2(keep_if_pos(v[i], hh & 0xFFFFu), keep_if_pos(v[i + 1], hh >> 16))
-                    : 0u;
+        w[e] = pack2((m >> (2 * e)) & 1u ? v[i] : 0.0f, (m >> (2 * e + 1)) & 1u ? v[i + 1] : 0.0f);
       }
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -578,6 +543,31 @@ int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cud
     case 16: return launch_f<16, false>(maps, a, num_sms, st);
     default: return (int)cudaErrorInvalidValue;
   }
+}
+
+__global__ void k_ray_records(GeoDev g, SourceArgs src, long long n_rays, int S, float *rec,
+                              float *ray_l, const float *proj, float *ray_p) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n_rays) return;
+  const Ray ray = source_ray(g, src, r);
+  const double step = ray.l / S;
+  const double s = ray.s0 + 0.5 * step;
+  float4 a = make_float4((float)ray.tbar, (float)((ray.oz + s * ray.dz) * g.zs + g.zb),
+                         (float)((ray.oy + s * ray.dy) * g.inv_R),
+                         (float)((ray.ox + s * ray.dx) * g.inv_R));
+  float4 b = make_float4((float)(step * ray.dz * g.zs), (float)(step * ray.dy * g.inv_R),
+                         (float)(step * ray.dx * g.inv_R), (float)ray.l);
+  reinterpret_cast<float4 *>(rec + 8 * r)[0] = a;
+  reinterpret_cast<float4 *>(rec + 8 * r)[1] = b;
+  if (ray_l) ray_l[r] = (float)ray.l;
+  if (ray_p) ray_p[r] = proj ? proj[src.idx[r]] : 0.0f;
+}
+
+void launch_ray_records(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
+                        float *rec, float *ray_l, const float *proj, float *ray_p,
+                        cudaStream_t st) {
+  k_ray_records<<<(int)((n_rays + 127) / 128), 128, 0, st>>>(g, src, n_rays, S, rec, ray_l, proj,
+                                                             ray_p);
 }
 
 int launch_bwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {

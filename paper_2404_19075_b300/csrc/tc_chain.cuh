@@ -34,12 +34,23 @@ struct ChainArgs {
   const float *w_out, *b_out;
   float *z_out;                    // [ns]
   float *ray_l, *ray_p;            // [n_rays]
+  const float *rays;               // per-ray records [n_rays][8] (ray sources), see
+                                   // launch_ray_records
+  uint32_t *masks[kChainMaxLayers];  // ReLU bits of h_L: [samples][W/32] words
   const float *proj;               // measured stack (training rays) or null
   // backward chain
   const float *dz;                 // dL/dz_out per sample
-  const __nv_bfloat16 *hs[kChainMaxLayers];  // forward outputs h_L (ReLU masks)
   int *err;
 };
+
+// Per-ray records for the forward chain, one thread per ray in FP64 (Sec. III
+// decode and rotation, FOV chord, App. A midpoints, App. B normalisation):
+// normalised time, normalised position of sample 0, normalised step between
+// samples (z, y, x each) and the chord length, as FP32 [n_rays][8]; also the
+// chord length and measured value of each ray.
+void launch_ray_records(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
+                        float *rec, float *ray_l, const float *proj, float *ray_p,
+                        cudaStream_t st);
 
 // Shared memory the chain needs for a width, layer-0 K and stage count.
 size_t chain_smem_bytes(int W, int k0, int stages);
@@ -47,8 +58,9 @@ int chain_stages(int W, int k0);
 bool chain_supports_freq(int F);
 int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st);
 // Backward chain (H >= 2): delta_{H-1} = dz w_out [h_{H-1} > 0], then
-// delta_{L-1} = (delta_L W_L) [h_{L-1} > 0] for L = H-1..1, all on chip;
-// every delta_L is stored through maps.h[L].
+// delta_{L-1} = (delta_L W_L) [h_{L-1} > 0] for L = H-1..1, all on chip, with
+// the ReLU bits the forward chain wrote to masks[L]; every delta_L is stored
+// through maps.h[L].
 int launch_bwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st);
 
 }  // namespace dinr

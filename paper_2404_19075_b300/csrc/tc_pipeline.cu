@@ -38,6 +38,8 @@ struct TcState {
   std::vector<int> kpad;
   __nv_bfloat16 *E = nullptr, *H = nullptr, *D0 = nullptr, *D1 = nullptr;
   __nv_bfloat16 *Dall = nullptr;  // [H][samples][W] deltas of every layer (chain path)
+  uint32_t *masks = nullptr;      // [H][samples][W/32] ReLU bits (chain path)
+  float *rec = nullptr;           // per-ray records [samples][8] (chain path)
   bool chain = false;
   float *zout = nullptr, *dz = nullptr, *ray_l = nullptr, *ray_p = nullptr, *pbar = nullptr,
         *sq = nullptr, *part = nullptr, *part_db = nullptr;
@@ -201,6 +203,13 @@ dinr_status chain(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S, b
   a.ray_p = proj ? t->ray_p : nullptr;
   a.proj = proj;
   a.err = t->err;
+  if (t->masks)
+    for (int L = 0; L < c->H; ++L) a.masks[L] = t->masks + (long long)L * ns * (c->W / 32);
+  if (src.kind == kSrcTrainRays || src.kind == kSrcVirtualView) {
+    launch_ray_records(c->geo, src, n_rays, S, t->rec, t->ray_l, proj, a.ray_p, c->st);
+    CKL();
+    a.rays = t->rec;
+  }
   double pw = (double)c->W * c->d_in + (double)(c->H - 1) * c->W * c->W + c->W;
   ProfScope ps(c, "tc_fwd_chain", 2.0 * ns * pw,
                store_h ? 2.0 * ns * (c->ldE + (double)c->H * c->W) : 4.0 * ns);
@@ -234,10 +243,10 @@ dinr_status bwd_chain(dinr_ctx *c, long long ns) {
   a.store_h = 1;
   a.w_out = c->d_params + c->offW[c->H];
   a.dz = t->dz;
-  for (int L = 0; L < c->H; ++L) a.hs[L] = hid(c, L, ns);
+  for (int L = 0; L < c->H; ++L) a.masks[L] = t->masks + (long long)L * ns * (c->W / 32);
   a.err = t->err;
   ProfScope ps(c, "tc_bwd_chain", 2.0 * ns * (double)(c->H - 1) * c->W * c->W,
-               2.0 * ns * c->W * (2.0 * c->H));
+               2.0 * ns * c->W * c->H + ns * (c->W / 8.0) * c->H + 4.0 * ns);
   int e = launch_bwd_chain(maps, a, t->num_sms, c->st);
   ++c->launches;
   if (e != 0)
@@ -355,8 +364,9 @@ bool tc_supported(const dinr_net *net) {
 }
 
 long long tc_bytes_per_sample(const dinr_ctx *c) {
-  long long deltas = chains_used(c) ? c->H : 2;
-  return 2LL * (c->ldE + (long long)(c->H + deltas) * c->W) + 8 + 16;
+  if (chains_used(c))
+    return 2LL * (c->ldE + 2LL * c->H * c->W) + (long long)c->H * c->W / 8 + 32 + 8 + 16;
+  return 2LL * (c->ldE + (long long)(c->H + 2) * c->W) + 8 + 16;
 }
 
 static bool chains_used(const dinr_ctx *c) { return chain_ok(c) && c->H >= 2; }
@@ -392,7 +402,9 @@ dinr_status tc_alloc(dinr_ctx *c) {
   t->part_floats = pf > pc ? pf : pc;
   t->chain = chains_used(c);
   if (t->chain)
-    ok = ok && grab((void **)&t->Dall, 2ull * ns * c->W * c->H);
+    ok = ok && grab((void **)&t->Dall, 2ull * ns * c->W * c->H) &&
+         grab((void **)&t->masks, 4ull * ns * (c->W / 32) * c->H) &&
+         grab((void **)&t->rec, 32ull * ns);
   else
     ok = ok && grab((void **)&t->D0, 2ull * ns * c->W) && grab((void **)&t->D1, 2ull * ns * c->W);
   ok = ok && grab((void **)&t->E, 2ull * ns * c->ldE) &&
