@@ -189,6 +189,47 @@ DINR_API dinr_status dinr_query(dinr_ctx *ctx, const float *coords_dev, int64_t 
 DINR_API dinr_status dinr_query_grid(dinr_ctx *ctx, double t, const double *lo,
                             const double *hi, const int *dims, float *out_dev);
 
+/* ----------------------------------------------------------------------
+ * Query server (Sec. V: inference from the trained network). Requests of
+ * different kinds and sizes are batched continuously: each dinr_serve_step
+ * runs one persistent launch over work taken from every in-flight request
+ * in arrival order (whole 128-sample tiles, whole rays), so large requests
+ * span several launches and requests that arrive in the meantime join the
+ * next one. Weights and per-request work lists stay on the device. BF16
+ * contexts whose shape runs the fused chain only (DINR_ERR_UNSUPPORTED
+ * otherwise).
+ * ---------------------------------------------------------------------- */
+enum { DINR_QUERY_POINTS = 0, DINR_QUERY_GRID = 1, DINR_QUERY_PROJECT = 2 };
+typedef struct {
+  int kind;                      /* DINR_QUERY_* */
+  const float *coords_dev;       /* POINTS: device float[n][4] (t, z, y, x) */
+  int64_t n;                     /* POINTS: number of points */
+  double t;                      /* GRID, PROJECT: time */
+  double lo[3], hi[3];           /* GRID: box (x, y, z), as dinr_query_grid */
+  int dims[3];                   /* GRID: (nx, ny, nz) */
+  double theta;                  /* PROJECT: angle */
+  int rows, cols, S;             /* PROJECT: detector and samples per ray */
+  float *out_dev;                /* device output, caller-owned: mu0*M per point /
+                                    voxel (z, y, x order) or p_bar per pixel
+                                    (row-major); valid once the request is done */
+} dinr_request;
+
+/* Batch size (samples per launch, rounded down to whole 128-sample tiles,
+ * at most the context's workspace) and the admission budget: requests are
+ * admitted while the outputs of in-flight requests fit max_inflight_bytes.
+ * 0 keeps the current value (defaults: the workspace; 4 GiB). */
+DINR_API dinr_status dinr_serve_config(dinr_ctx *ctx, int64_t max_batch_samples,
+                                       int64_t max_inflight_bytes);
+/* Admit a request. *id receives its handle. DINR_ERR_BUSY: the in-flight
+ * budget is full (nothing was admitted; retry after requests complete).
+ * The request's input and output memory must stay valid until it is done. */
+DINR_API dinr_status dinr_serve_submit(dinr_ctx *ctx, const dinr_request *req, int64_t *id);
+/* Launch one batch (no wait). *in_flight receives the number of admitted
+ * requests not yet complete. */
+DINR_API dinr_status dinr_serve_step(dinr_ctx *ctx, int *in_flight);
+/* *done = 1 once request id has completed on the GPU (reported once). */
+DINR_API dinr_status dinr_serve_poll(dinr_ctx *ctx, int64_t id, int *done);
+
 /* Copy parameters in or out (FP32, flat layout above); on_device selects
  * whether the caller's pointer is a device pointer. Setting parameters does
  * not reset the Adam moments. */

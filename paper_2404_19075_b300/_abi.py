@@ -48,6 +48,15 @@ class Train(C.Structure):
                 ("sampler_seed", C.c_uint64)]
 
 
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("coords_dev", C.c_void_p), ("n", C.c_int64),
+                ("t", C.c_double), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("dims", C.c_int * 3), ("theta", C.c_double), ("rows", C.c_int),
+                ("cols", C.c_int), ("S", C.c_int), ("out_dev", C.c_void_p)]
+
+
+QUERY = {"points": 0, "grid": 1, "project": 2}
+
 vp, i64 = C.c_void_p, C.c_int64
 PROTOTYPES = {
     "dinr_param_count": (C.c_int64, [C.c_int, C.c_int, C.c_int]),
@@ -72,6 +81,10 @@ PROTOTYPES = {
                                        C.c_double, vp, i64, vp, vp]),
     "dinr_phantom_project_noalloc": (C.c_int, [C.POINTER(Geometry), C.c_int, vp, vp, vp, vp,
                                                C.c_double, vp, i64, vp, vp]),
+    "dinr_serve_config": (C.c_int, [vp, i64, i64]),
+    "dinr_serve_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    "dinr_serve_step": (C.c_int, [vp, C.POINTER(C.c_int)]),
+    "dinr_serve_poll": (C.c_int, [vp, i64, C.POINTER(C.c_int)]),
     "dinr_profile": (C.c_int, [vp, C.c_int]),
     "dinr_profile_report": (C.c_int, [vp, C.c_char_p, C.c_size_t]),
     "dinr_synchronize": (C.c_int, [vp]),

@@ -285,6 +285,7 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
 void dinr_destroy(dinr_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
+  dinr_serve_release(c);
   destroy_backend(c);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   for (void *p : c->allocs) cudaFree(p);

@@ -50,6 +50,8 @@ struct dinr_ctx {
 
   // BF16 (tensor-core) backend state, owned by the tensor-core pipeline.
   void *tc = nullptr;
+  // query server state (serve.cu)
+  void *serve = nullptr;
 
   // per-kernel event timing (dinr_profile)
   bool prof = false;
@@ -65,6 +67,7 @@ struct dinr_ctx {
 };
 
 int dinr_fail(dinr_ctx *c, int status, const char *fmt, ...);
+void dinr_serve_release(dinr_ctx *c);
 
 // Brackets the launches issued in its scope with two events on the context
 // stream when profiling is on.

@@ -151,47 +151,13 @@ __device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
   mbar_wait(s.drain, 0, p.err, 14);
 }
 
-// Layer-0 input of one tile: the Fourier features of its 128 samples, in
-// the K-chunks this warp owns (chunks half, half + 2, ...). F is a template
-// parameter so that every feature lands in a register by static index.
-// Octave features use exact sincospif at octaves 0, 4, 8, ... and angle
-// doubling in between (error about 1e-6, far below BF16 resolution).
+// The features of a sample with normalised coordinates c (FP32) into the
+// K-chunks this warp owns, in the 128B-swizzled layout the MMA reads.
 template <int F>
-__device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *A,
-                            long long tile, int q, int half, int lane) {
+__device__ __forceinline__ void write_features(uint8_t *A, const float (&c)[4], bool live,
+                                               int r_in, int half) {
   constexpr int kDin = 4 + 8 * F;
   constexpr int kChunks = (kDin + 63) / 64;
-  const int r_in = q * 32 + lane;
-  const long long smp = tile * 128 + r_in;
-  const bool live = smp < p.ns;
-  const bool ray_src = p.src.kind == kSrcTrainRays || p.src.kind == kSrcVirtualView;
-  // Normalised (t, z, y, x) in FP32. A ray is set up once in FP64 (chord,
-  // normalised start point of its first sample and normalised step); its
-  // samples are then start + j * step in FP32, whose rounding (about 1e-7)
-  // moves the phase of the highest octave by under 1e-3 rad, below BF16
-  // resolution of the features.
-  float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  if (ray_src) {
-    const long long s0 = live ? smp : 0;
-    const long long r = s0 / p.S;
-    const int j = (int)(s0 - r * p.S);
-    if (live) {
-      // tbar, start (z, y, x), step (z, y, x), chord length
-      const float4 a = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r));
-      const float4 b = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r) + 1);
-      c[0] = a.x;
-      c[1] = fmaf((float)j, b.x, a.y);
-      c[2] = fmaf((float)j, b.y, a.z);
-      c[3] = fmaf((float)j, b.z, a.w);
-    }
-  } else if (live) {
-    double cd[4];
-    float len;
-    source_coords(p.g, p.src, smp, 0, 1, cd, &len);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) c[k] = (float)cd[k];
-    if (half == 0 && p.ray_l) p.ray_l[smp] = 1.0f;
-  }
 #pragma unroll
   for (int jc = 0; jc < kChunks; ++jc) {
     if ((jc & 1) != half) continue;
@@ -204,8 +170,6 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      constexpr int dummy = 0;
-      (void)dummy;
       const int lo_col = 4 + 2 * F * k;
       if (lo_col + 2 * F <= 64 * jc || lo_col >= 64 * (jc + 1)) continue;
       const float hi = c[k];
@@ -236,10 +200,90 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) =
           make_uint4(w[4 * c16], w[4 * c16 + 1], w[4 * c16 + 2], w[4 * c16 + 3]);
   }
+}
+
+// Coordinates of one training / re-projection / point sample (single source).
+template <int F>
+__device__ __forceinline__ void tile_features(const ChainArgs &p, uint8_t *A, long long tile,
+                                              long long smp, bool live, int r_in, int q,
+                                              int half, int lane) {
+  const bool ray_src = p.src.kind == kSrcTrainRays || p.src.kind == kSrcVirtualView;
+  // Normalised (t, z, y, x) in FP32. A ray is set up once in FP64 (chord,
+  // normalised start point of its first sample and normalised step); its
+  // samples are then start + j * step in FP32, whose rounding (about 1e-7)
+  // moves the phase of the highest octave by under 1e-3 rad, below BF16
+  // resolution of the features.
+  float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (ray_src) {
+    const long long s0 = live ? smp : 0;
+    const long long r = s0 / p.S;
+    const int j = (int)(s0 - r * p.S);
+    if (live) {
+      // tbar, start (z, y, x), step (z, y, x), chord length
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r));
+      const float4 b = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r) + 1);
+      c[0] = a.x;
+      c[1] = fmaf((float)j, b.x, a.y);
+      c[2] = fmaf((float)j, b.y, a.z);
+      c[3] = fmaf((float)j, b.z, a.w);
+    }
+  } else if (live) {
+    double cd[4];
+    float len;
+    source_coords(p.g, p.src, smp, 0, 1, cd, &len);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = (float)cd[k];
+    if (half == 0 && p.ray_l) p.ray_l[smp] = 1.0f;
+  }
+  write_features<F>(A, c, live, r_in, half);
+}
+
+
+// Layer-0 input of one tile: the Fourier features of its 128 samples, in
+// the K-chunks this warp owns (chunks half, half + 2, ...). F is a template
+// parameter so that every feature lands in a register by static index.
+// Octave features use exact sincospif at octaves 0, 4, 8, ... and angle
+// doubling in between (error about 1e-6, far below BF16 resolution).
+template <int F>
+__device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *A,
+                            long long tile, int q, int half, int lane) {
+  const int r_in = q * 32 + lane;
+  long long smp = tile * 128 + r_in;
+  bool live = smp < p.ns;
+  if (p.items && live) {
+    // serving batch: the tile's work item decides what its samples are
+    const WorkItem &wi = p.items[p.tile_item[tile]];
+    const long long local = (tile - wi.tile0) * 128 + r_in;
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (local < wi.n) {
+      if (wi.kind == kSrcVirtualView) {
+        const long long r = wi.rec0 + local / wi.S;
+        const int j = (int)(local % wi.S);
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r) + 1);
+        c[0] = a.x;
+        c[1] = fmaf((float)j, b.x, a.y);
+        c[2] = fmaf((float)j, b.y, a.z);
+        c[3] = fmaf((float)j, b.z, a.w);
+      } else {
+        double cd[4];
+        float len;
+        source_coords(p.g, wi.src, local, 0, 1, cd, &len);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = (float)cd[k];
+        if (half == 0 && p.ray_l) p.ray_l[smp] = 1.0f;
+      }
+    } else {
+      live = false;
+    }
+    write_features<F>(A, c, live, r_in, half);
+  } else {
+    tile_features<F>(p, A, tile, smp, live, r_in, q, half, lane);
+  }
   fence_async_smem();
   __syncwarp();
   if (lane == 0 && p.store_h && tile * 128 + q * 32 < p.ns) {
-    for (int jc = half; jc < kChunks; jc += 2)
+    for (int jc = half; jc < (4 + 8 * F + 63) / 64; jc += 2)
       tma_store_2d(&maps.e, A + (size_t)jc * kChunkBytes + q * 32 * 128, 64 * jc,
                    (int)(tile * 128 + q * 32));
     bulk_commit();

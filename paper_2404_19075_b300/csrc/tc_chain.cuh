@@ -11,6 +11,17 @@ namespace dinr {
 
 constexpr int kChainMaxLayers = 8;
 
+// One piece of a serving batch: samples [0, n) of a query, starting at tile
+// tile0 of the batch (items start on 128-sample tile boundaries).
+struct WorkItem {
+  int kind;          // kSrcVirtualView (rays from records) or kSrcPoints / kSrcGrid
+  int S;             // samples per ray (rays), 1 otherwise
+  long long tile0;   // first tile of the item in the batch
+  long long n;       // samples of the item in this batch
+  long long rec0;    // first ray record of the item (rays)
+  SourceArgs src;    // points / grid source, `first` = offset within the query
+};
+
 struct ChainMaps {
   // forward: BF16 weights W_L [W][K_L]; backward: transposed W_L^T [W][W]; box {64, W}
   CUtensorMap w[kChainMaxLayers];
@@ -38,6 +49,9 @@ struct ChainArgs {
                                    // launch_ray_records
   uint32_t *masks[kChainMaxLayers];  // ReLU bits of h_L: [samples][W/32] words
   const float *proj;               // measured stack (training rays) or null
+  // serving batches: per-tile work items (null for a single source)
+  const WorkItem *items;
+  const int *tile_item;            // [m_tiles] item of each tile
   // backward chain
   const float *dz;                 // dL/dz_out per sample
   int *err;

@@ -40,6 +40,7 @@ struct TcState {
   __nv_bfloat16 *Dall = nullptr;  // [H][samples][W] deltas of every layer (chain path)
   uint32_t *masks = nullptr;      // [H][samples][W/32] ReLU bits (chain path)
   float *rec = nullptr;           // per-ray records [samples][8] (chain path)
+  float *ones = nullptr;          // 1.0 [samples], allocated when serving starts
   bool chain = false;
   float *zout = nullptr, *dz = nullptr, *ray_l = nullptr, *ray_p = nullptr, *pbar = nullptr,
         *sq = nullptr, *part = nullptr, *part_db = nullptr;
@@ -537,4 +538,77 @@ dinr_status tc_forward_rays(dinr_ctx *c, const SourceArgs &src, long long n_rays
 
 dinr_status tc_forward_points(dinr_ctx *c, const SourceArgs &src, long long n, float *out) {
   return tc_forward(c, src, n, 1, out);
+}
+
+// ------------------------------------------------------------------ serving
+
+struct ServeBackend {
+  float *zout, *rec, *ray_l;
+  const float *ones;
+  long long capacity;
+};
+
+__global__ void k_fill(float *p, long long n, float v) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+bool tc_serve_backend(dinr_ctx *c, ServeBackend *b) {
+  TcState *t = S_(c);
+  if (!t || !t->chain) return false;
+  long long ns = (long long)c->chunk_rays * c->S;
+  if (!t->ones) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, sizeof(float) * ns) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    c->allocs.push_back(p);
+    t->ones = (float *)p;
+    k_fill<<<ceil_div(ns, 256), 256, 0, c->st>>>(t->ones, ns, 1.0f);
+  }
+  b->zout = t->zout;
+  b->rec = t->rec;
+  b->ray_l = t->ray_l;
+  b->ones = t->ones;
+  b->capacity = ns;
+  return true;
+}
+
+dinr_status tc_serve_chain(dinr_ctx *c, const WorkItem *items, const int *tile_item,
+                           long long m_tiles) {
+  TcState *t = S_(c);
+  ChainMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  bool ok = true;
+  for (int L = 0; L < c->H; ++L)
+    ok = ok && make_tmap_bf16(&maps.w[L], t->Wb[L], c->W, t->kpad[L], t->kpad[L], c->W);
+  if (!ok) return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "tensor map encoding failed (serve)");
+  ChainArgs a{};
+  a.g = c->geo;
+  a.F = c->F;
+  a.d_in = c->d_in;
+  a.k0 = chain_k0(c);
+  a.W = c->W;
+  a.H = c->H;
+  a.ns = m_tiles * 128;
+  a.m_tiles = (int)m_tiles;
+  a.stages = chain_stages(c->W, a.k0);
+  a.store_h = 0;
+  for (int L = 0; L < c->H; ++L) a.bias[L] = c->d_params + c->offb[L];
+  a.w_out = c->d_params + c->offW[c->H];
+  a.b_out = c->d_params + c->offb[c->H];
+  a.z_out = t->zout;
+  a.rays = t->rec;
+  a.items = items;
+  a.tile_item = tile_item;
+  a.err = t->err;
+  double pw = (double)c->W * c->d_in + (double)(c->H - 1) * c->W * c->W + c->W;
+  ProfScope ps(c, "tc_serve_chain", 2.0 * a.ns * pw, 4.0 * a.ns);
+  int e = launch_fwd_chain(maps, a, t->num_sms, c->st);
+  ++c->launches;
+  if (e != 0)
+    return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "serving chain launch: %s",
+                                  cudaGetErrorString((cudaError_t)e));
+  return DINR_OK;
 }

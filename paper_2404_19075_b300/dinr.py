@@ -182,6 +182,49 @@ class Dinr:
         self._c(_abi.lib().dinr_query_grid(self._h, float(t), lo_a, hi_a, d_a, _ptr(out)))
         return out.view(dims[2], dims[1], dims[0])
 
+    # -- query server (continuous batching)
+    def serve_config(self, max_batch_samples=0, max_inflight_bytes=0):
+        self._c(_abi.lib().dinr_serve_config(self._h, int(max_batch_samples),
+                                             int(max_inflight_bytes)))
+
+    def serve_submit(self, kind, out, coords=None, t=0.0, lo=(0, 0, 0), hi=(0, 0, 0),
+                     dims=(1, 1, 1), theta=0.0, rows=0, cols=0, S=0):
+        """Admit a query writing into the CUDA tensor `out`; returns its id,
+        or None when the in-flight budget is full (retry later)."""
+        r = _abi.Request()
+        r.kind = _abi.QUERY[kind]
+        keep = [out]
+        if kind == "points":
+            ct = _cuda_f32(coords).view(-1, 4)
+            keep.append(ct)
+            r.coords_dev, r.n = ct.data_ptr(), ct.shape[0]
+        r.t = float(t)
+        r.lo = (C.c_double * 3)(*lo)
+        r.hi = (C.c_double * 3)(*hi)
+        r.dims = (C.c_int * 3)(*dims)
+        r.theta, r.rows, r.cols, r.S = float(theta), rows, cols, S
+        r.out_dev = out.data_ptr()
+        rid = C.c_int64()
+        st = _abi.lib().dinr_serve_submit(self._h, C.byref(r), C.byref(rid))
+        if st == _abi.ERR_BUSY:
+            return None
+        self._c(st)
+        self._serving = getattr(self, "_serving", {})
+        self._serving[rid.value] = keep
+        return rid.value
+
+    def serve_step(self) -> int:
+        n = C.c_int()
+        self._c(_abi.lib().dinr_serve_step(self._h, C.byref(n)))
+        return n.value
+
+    def serve_poll(self, rid) -> bool:
+        d = C.c_int()
+        self._c(_abi.lib().dinr_serve_poll(self._h, int(rid), C.byref(d)))
+        if d.value:
+            self._serving.pop(rid, None)
+        return bool(d.value)
+
     # -- state
     def params(self):
         out = torch.empty(self.n_params, device="cuda")
