@@ -8,7 +8,10 @@ Workload: parallel beam, 512 views over 4 rotations, 128 x 128 detector,
 65,536 rays per step (8,388,608 samples); 16 moving, growing ellipsoids
 give the measurements. A step is the whole hot path: minibatch draw, ray
 generation, encoding, MLP forward, forward model and loss, backward, Adam.
-Metric: training ray-samples per second (whole job over all ranks).
+Metric: training ray-samples per second (whole job over all ranks). A
+serving leg replays a seeded Poisson stream of mixed queries (time slices,
+sub-volumes, re-projections) against the query server of a cone-beam 6 x 256
+network and adds p50/p99 latency and outputs/s under "serving".
 
 Our arm runs the library (default BF16 tensor-core path; the plain FP32 path
 is timed beside it). The reference arm (--impl reference) times the FP64 CPU
@@ -247,11 +250,63 @@ def run_ours(args):
         results[prec] = dict(dt=dt, steps=steps, prof=prof, clocks=ck.summary(), loss=loss,
                              e2e=ws * e2e_steps * B * S / e2e_dt)
         m.close()
+    if args.serve_queries > 0:
+        try:
+            results["serving"] = run_serving(args, rank)
+        except Exception as e:                       # reported, not hidden
+            results["serving"] = {"error": repr(e)}
     if rank == 0:
         emit(args, w, results, ws)
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_serving(args, rank):
+    """Query serving on the cone-beam 6x256 network: a seeded Poisson stream
+    of mixed time slices, sub-volumes and re-projections (256^2 detector,
+    256 samples per ray) replayed against the continuous-batching server.
+    Weights are the seeded initialisation of that architecture."""
+    import torch
+
+    from paper_2404_19075_b300 import Dinr, serving
+    from synthetic import workloads as wl
+
+    w = wl.workload(5)
+    g, net = w.geom, w.net
+    proj = torch.zeros(g.n_proj, device="cuda")
+    theta = wl.he_init(net, w.seeds["weights"]).astype(np.float32)
+    m = Dinr(g, net, replace(w.train, batch_rays=8192), proj, prec="bf16", init_params=theta)
+    m.serve_config(max_batch_samples=args.serve_batch)
+    warm = wl.query_stream(6, rate=1e6, seed=4999)
+    serving.run(m, warm)
+    qs = wl.query_stream(args.serve_queries, rate=args.serve_rate, seed=5000 + rank)
+    m.profile(True)
+    with Clocks(torch.cuda.current_device()) as ck:
+        res = serving.run(m, qs, time_limit=120.0)
+    m.profile(False)
+    prof = m.profile_report()
+    m.close()
+    chain = prof.get("tc_serve_chain", {"ms": float("nan"), "flops": 0, "launches": 0})
+    pk, src = peaks()
+    tf = chain["flops"] / (chain["ms"] / 1e3) / 1e12 if chain["ms"] else None
+    kinds = {k: sum(1 for q in qs if q.kind == k) for k in ("slice", "subvolume", "reprojection")}
+    return {"metric": "query voxels/s (outputs: voxels and detector pixels)",
+            "value": res["outputs_per_s"], "unit": "outputs/s",
+            "samples_per_s": res["samples_per_s"],
+            "p50_ms": res.get("p50_ms"), "p99_ms": res.get("p99_ms"),
+            "queries": len(qs), "completed": res["completed"], "wall_s": res["wall"],
+            "arrival_rate_per_s": args.serve_rate, "mix": kinds,
+            "arrivals_span_s": qs[-1].arrival,
+            "max_batch_samples": args.serve_batch,
+            "chain": {"launches": chain["launches"], "ms": chain["ms"], "tflops": tf,
+                      "frac_of_bf16_sustained": tf / pk["bf16_tflops_sustained"] if tf else None,
+                      "peak_source": f"bf16_tflops_sustained ({src})"},
+            "gpu_launches": prof.get("total_launches", {}).get("launches"),
+            "clocks": ck.summary(),
+            "config": "cone beam SOD 4 / SDD 8, MLP 6x256 ReLU, 10-octave encoding; "
+                      "slices 128^2..1024^2, sub-volumes 32^3..256^3, re-projections "
+                      "256^2 x 256 samples; seeded Poisson arrivals"}
 
 
 def emit(args, w, results, ws):
@@ -294,6 +349,9 @@ def emit(args, w, results, ws):
             "e2e": {"value": main["e2e"], "unit": "samples/s", "h2d_bytes_per_step": 8 * B,
                     "d2h_bytes_per_step": 4},
             "loss_last": main["loss"]}
+    serving = results.pop("serving", None)
+    if serving is not None:
+        line["serving"] = serving
     for p, r in results.items():
         if p != args.prec:
             line[f"{p}_path"] = ({"error": r["error"]} if "error" in r else
@@ -316,6 +374,11 @@ def main():
     ap.add_argument("--rays", type=int, default=0,
                     help="rays per step (default: the workload's 65,536); smaller batches "
                          "are for profiler captures, not bench lines")
+    ap.add_argument("--serve-queries", type=int, default=200,
+                    help="queries of the serving leg (0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
+    ap.add_argument("--serve-batch", type=int, default=1 << 21,
+                    help="samples per serving launch at most")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -185,6 +185,7 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_UNSUPPORTED,
                                   "the BF16 path does not support this network shape");
 
+  cudaGetLastError();  // a stale error of an earlier call is not this context's
   dinr_ctx *c = new (std::nothrow) dinr_ctx();
   if (!c) return (dinr_status)dinr_fail(nullptr, DINR_ERR_OOM, "host allocation failed");
   c->st = (cudaStream_t)cuda_stream;

@@ -61,8 +61,13 @@ struct Server {
   std::vector<cudaEvent_t> pool;
   WorkItem *items_dev = nullptr;
   int *tile_item_dev = nullptr;
-  WorkItem *items_host = nullptr;      // pinned staging
-  int *tile_item_host = nullptr;
+  // pinned staging of the work list, a ring of slots: a slot is rewritten
+  // only after the copy that read it has run (its event)
+  static constexpr int kSlots = 4;
+  WorkItem *items_host = nullptr;      // [kSlots][max_items]
+  int *tile_item_host = nullptr;       // [kSlots][max_tiles]
+  cudaEvent_t slot_event[kSlots] = {};
+  int slot = 0;
   long long max_items = 0, max_tiles = 0;
   ServeBackend be{};
 };
@@ -139,10 +144,14 @@ dinr_status dinr_serve_config(dinr_ctx *c, int64_t max_batch_samples, int64_t ma
     sv->items_dev = (WorkItem *)p;
     ok = ok && cudaMalloc(&p, sizeof(int) * sv->max_tiles) == cudaSuccess;
     sv->tile_item_dev = (int *)p;
-    ok = ok && cudaMallocHost(&p, sizeof(WorkItem) * sv->max_items) == cudaSuccess;
+    ok = ok && cudaMallocHost(&p, sizeof(WorkItem) * sv->max_items * Server::kSlots) ==
+                   cudaSuccess;
     sv->items_host = (WorkItem *)p;
-    ok = ok && cudaMallocHost(&p, sizeof(int) * sv->max_tiles) == cudaSuccess;
+    ok = ok && cudaMallocHost(&p, sizeof(int) * sv->max_tiles * Server::kSlots) == cudaSuccess;
     sv->tile_item_host = (int *)p;
+    for (int i = 0; i < Server::kSlots; ++i)
+      ok = ok && cudaEventCreateWithFlags(&sv->slot_event[i], cudaEventDisableTiming) ==
+                     cudaSuccess;
     c->serve = sv;
     if (!ok) {
       cudaGetLastError();
@@ -163,6 +172,8 @@ void dinr_serve_release(dinr_ctx *c) {
   cudaStreamSynchronize(c->st);
   for (auto &r : sv->launched) cudaEventDestroy(r.done_event);
   for (auto e : sv->pool) cudaEventDestroy(e);
+  for (auto e : sv->slot_event)
+    if (e) cudaEventDestroy(e);
   cudaFree(sv->items_dev);
   cudaFree(sv->tile_item_dev);
   cudaFreeHost(sv->items_host);
@@ -214,6 +225,12 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
     int n_items = 0;
     std::vector<size_t> finished;
     std::vector<long long> first_unit(sv->active.size());
+    // the staging slot's previous copy must have run before it is rewritten
+    const int slot = sv->slot;
+    sv->slot = (slot + 1) % Server::kSlots;
+    CK(cudaEventSynchronize(sv->slot_event[slot]));
+    WorkItem *items_host = sv->items_host + (size_t)slot * sv->max_items;
+    int *tile_item_host = sv->tile_item_host + (size_t)slot * sv->max_tiles;
     for (size_t k = 0; k < sv->active.size() && n_items < sv->max_items; ++k) {
       Request &r = sv->active[k];
       long long room = sv->max_batch - tiles * 128;
@@ -222,7 +239,7 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
       if (fit <= 0) break;
       if (units > fit) units = fit;
       long long n = units * r.unit;
-      WorkItem &w = sv->items_host[n_items];
+      WorkItem &w = items_host[n_items];
       w = WorkItem{};
       w.kind = r.q.kind == DINR_QUERY_PROJECT ? kSrcVirtualView : source_of(c, r.q).kind;
       w.S = (int)r.unit;
@@ -232,7 +249,7 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
       w.src = source_of(c, r.q);
       w.src.first = r.next / r.unit;  // first ray / point of this piece
       long long nt = (n + 127) / 128;
-      for (long long t = 0; t < nt; ++t) sv->tile_item_host[tiles + t] = n_items;
+      for (long long t = 0; t < nt; ++t) tile_item_host[tiles + t] = n_items;
       first_unit[k] = r.next / r.unit;
       tiles += nt;
       if (w.kind == kSrcVirtualView) rec += units;
@@ -241,13 +258,14 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
       if (r.next >= r.samples) finished.push_back(k);
     }
     if (n_items > 0) {
-      CK(cudaMemcpyAsync(sv->items_dev, sv->items_host, sizeof(WorkItem) * n_items,
+      CK(cudaMemcpyAsync(sv->items_dev, items_host, sizeof(WorkItem) * n_items,
                          cudaMemcpyHostToDevice, c->st));
-      CK(cudaMemcpyAsync(sv->tile_item_dev, sv->tile_item_host, sizeof(int) * tiles,
+      CK(cudaMemcpyAsync(sv->tile_item_dev, tile_item_host, sizeof(int) * tiles,
                          cudaMemcpyHostToDevice, c->st));
+      CK(cudaEventRecord(sv->slot_event[slot], c->st));
       // ray records of the re-projection pieces
       for (int i = 0; i < n_items; ++i) {
-        const WorkItem &w = sv->items_host[i];
+        const WorkItem &w = items_host[i];
         if (w.kind != kSrcVirtualView) continue;
         launch_ray_records(c->geo, w.src, w.n / w.S, w.S, sv->be.rec + 8 * w.rec0,
                            sv->be.ray_l + w.rec0, nullptr, nullptr, c->st);
@@ -258,7 +276,7 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
       // forward model of each piece into the request's output
       size_t k = 0;
       for (int i = 0; i < n_items; ++i, ++k) {
-        const WorkItem &w = sv->items_host[i];
+        const WorkItem &w = items_host[i];
         Request &r = sv->active[k];
         const float *z = sv->be.zout + w.tile0 * 128;
         if (w.kind == kSrcVirtualView) {
@@ -271,22 +289,22 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
         ++c->launches;
       }
       CK(cudaGetLastError());
-      cudaEvent_t ev;
-      if (!sv->pool.empty()) {
-        ev = sv->pool.back();
-        sv->pool.pop_back();
-      } else {
-        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      }
-      CK(cudaEventRecord(ev, c->st));
-      // completely launched requests leave the active list, newest first
+      // completely launched requests leave the active list, newest first; each
+      // owns one event recorded after this batch
       for (size_t f = finished.size(); f-- > 0;) {
+        cudaEvent_t ev;
+        if (!sv->pool.empty()) {
+          ev = sv->pool.back();
+          sv->pool.pop_back();
+        } else {
+          CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        }
+        CK(cudaEventRecord(ev, c->st));
         Request r = sv->active[finished[f]];
         r.done_event = ev;
         sv->launched.push_back(r);
         sv->active.erase(sv->active.begin() + (long)finished[f]);
       }
-      if (finished.empty()) sv->pool.push_back(ev);  // nothing waits on it
     }
   }
   if (in_flight) *in_flight = (int)(sv->active.size() + sv->launched.size());
