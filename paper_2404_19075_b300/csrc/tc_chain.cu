@@ -67,6 +67,66 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
+// Packed FP32 add of two pairs (one instruction on sm_100 and later).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<uint64_t *>(&a)), "l"(*reinterpret_cast<uint64_t *>(&b)));
+  return *reinterpret_cast<float2 *>(&d);
+}
+
+// BF16 pair (lo, hi) of max(x, 0), rounded to nearest even.
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// L1 policy. With nearly all of the SM's shared memory in use the L1 cache
+// is small: the per-layer vectors every tile reads (biases, output weights)
+// are loaded with evict_last, and the per-sample streams (ReLU bits, ray
+// records) bypass L1 so that they do not evict them.
+__device__ __forceinline__ float4 ld_keep(const float *p) {
+  float4 v;
+  asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_stream4(const float *p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream2(const uint32_t *p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_stream2(uint32_t *p, uint2 v) {
+  asm volatile("st.global.L1::no_allocate.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(v.x), "r"(v.y)
+               : "memory");
+}
+
+// ReLU bits. Of the 32 columns of a mask word, the pair (2k, 2k+1) sits at
+// bits 15-k and 31-k, so that one integer add flags both halves of a packed
+// BF16 pair: for non-negative halves (sign cleared), adding 0x7FFF sets bit
+// 15 of a half exactly when the half is nonzero, with no carry out of it.
+__device__ __forceinline__ uint32_t pair_flags(uint32_t w, int k) {
+  return (((w & 0x7FFF7FFFu) + 0x7FFF7FFFu) & 0x80008000u) >> k;
+}
+// 0xFFFF in each half of a BF16 pair whose bit is set in mask word m (pair k).
+__device__ __forceinline__ uint32_t pair_mask(uint32_t m, int k) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %1, 0xBB99;" : "=r"(d) : "r"(m << k));
+  return d;
+}
+
 // Tiles of this CTA: blockIdx.x + k * gridDim.x, processed in pairs.
 __device__ __forceinline__ long long tile_of(const ChainArgs &p, int pair, int slot) {
   return (long long)blockIdx.x + (long long)(2 * pair + slot) * gridDim.x;
@@ -220,8 +280,8 @@ __device__ __forceinline__ void tile_features(const ChainArgs &p, uint8_t *A, lo
     const int j = (int)(s0 - r * p.S);
     if (live) {
       // tbar, start (z, y, x), step (z, y, x), chord length
-      const float4 a = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r));
-      const float4 b = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r) + 1);
+      const float4 a = ld_stream4(p.rays + 8 * r);
+      const float4 b = ld_stream4(p.rays + 8 * r + 4);
       c[0] = a.x;
       c[1] = fmaf((float)j, b.x, a.y);
       c[2] = fmaf((float)j, b.y, a.z);
@@ -259,8 +319,8 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
       if (wi.kind == kSrcVirtualView) {
         const long long r = wi.rec0 + local / wi.S;
         const int j = (int)(local % wi.S);
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r));
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(p.rays + 8 * r) + 1);
+        const float4 a = ld_stream4(p.rays + 8 * r);
+        const float4 b = ld_stream4(p.rays + 8 * r + 4);
         c[0] = a.x;
         c[1] = fmaf((float)j, b.x, a.y);
         c[2] = fmaf((float)j, b.y, a.z);
@@ -304,47 +364,38 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
   uint8_t *A = s.A[slot];
   float dot = 0.0f;
   for (int jc = half; jc < p.W / 64; jc += 2) {
+    // bias of the chunk first, so that its load overlaps the TMEM load
+    float4 bb[16];
+#pragma unroll
+    for (int i4 = 0; i4 < 16; ++i4) bb[i4] = ld_keep(bias + 64 * jc + 4 * i4);
     float v[64];
-    tmem_ld32(trow + 64 * jc, *reinterpret_cast<float(*)[32]>(v));
-    tmem_ld32(trow + 64 * jc + 32, *reinterpret_cast<float(*)[32]>(v + 32));
-    const float4 *b4 = reinterpret_cast<const float4 *>(bias + 64 * jc);
+    tmem_ld64(trow + 64 * jc, v);
+    uint32_t w[32];
+    uint32_t bits[2] = {0u, 0u};
 #pragma unroll
     for (int i4 = 0; i4 < 16; ++i4) {
-      const float4 b = __ldg(b4 + i4);
-      v[4 * i4] = fmaxf(v[4 * i4] + b.x, 0.0f);
-      v[4 * i4 + 1] = fmaxf(v[4 * i4 + 1] + b.y, 0.0f);
-      v[4 * i4 + 2] = fmaxf(v[4 * i4 + 2] + b.z, 0.0f);
-      v[4 * i4 + 3] = fmaxf(v[4 * i4 + 3] + b.w, 0.0f);
-    }
-    if (last) {
-      const float4 *o4 = reinterpret_cast<const float4 *>(p.w_out + 64 * jc);
-#pragma unroll
-      for (int i4 = 0; i4 < 16; ++i4) {
-        const float4 o = __ldg(o4 + i4);
-        dot = fmaf(v[4 * i4], o.x, dot);
-        dot = fmaf(v[4 * i4 + 1], o.y, dot);
-        dot = fmaf(v[4 * i4 + 2], o.z, dot);
-        dot = fmaf(v[4 * i4 + 3], o.w, dot);
+      const float4 b = bb[i4];
+      const float2 s0 = add2(make_float2(v[4 * i4], v[4 * i4 + 1]), make_float2(b.x, b.y));
+      const float2 s1 = add2(make_float2(v[4 * i4 + 2], v[4 * i4 + 3]), make_float2(b.z, b.w));
+      w[2 * i4] = pack2_relu(s0.x, s0.y);
+      w[2 * i4 + 1] = pack2_relu(s1.x, s1.y);
+      bits[i4 >> 3] |= pair_flags(w[2 * i4], (2 * i4) & 15);
+      bits[i4 >> 3] |= pair_flags(w[2 * i4 + 1], (2 * i4 + 1) & 15);
+      if (last) {
+        const float4 o = ld_keep(p.w_out + 64 * jc + 4 * i4);
+        dot = fmaf(fmaxf(s0.x, 0.0f), o.x, dot);
+        dot = fmaf(fmaxf(s0.y, 0.0f), o.y, dot);
+        dot = fmaf(fmaxf(s1.x, 0.0f), o.z, dot);
+        dot = fmaf(fmaxf(s1.y, 0.0f), o.w, dot);
       }
     }
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
-    uint32_t bits[2] = {0u, 0u};
 #pragma unroll
-    for (int c16 = 0; c16 < 8; ++c16) {
-      uint32_t w[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        w[e] = pack2(v[8 * c16 + 2 * e], v[8 * c16 + 2 * e + 1]);
-        // ReLU bit of each stored BF16 value: nonzero (it is never negative)
-        const int b = 8 * c16 + 2 * e;
-        bits[b >> 5] |= ((w[e] & 0xFFFFu) ? 1u : 0u) << (b & 31);
-        bits[b >> 5] |= ((w[e] >> 16) ? 1u : 0u) << ((b + 1) & 31);
-      }
-      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
+    for (int c16 = 0; c16 < 8; ++c16)
+      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) =
+          make_uint4(w[4 * c16], w[4 * c16 + 1], w[4 * c16 + 2], w[4 * c16 + 3]);
     if (live && p.masks[L])
-      *reinterpret_cast<uint2 *>(p.masks[L] + row * (p.W / 32) + 2 * jc) =
-          make_uint2(bits[0], bits[1]);
+      st_stream2(p.masks[L] + row * (p.W / 32) + 2 * jc, make_uint2(bits[0], bits[1]));
   }
   fence_async_smem();
   __syncwarp();
@@ -395,19 +446,18 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
   const float dzr = live ? p.dz[row] : 0.0f;
   const uint32_t *mrow = p.masks[p.H - 1] + (live ? row : 0) * (p.W / 32);
   for (int jc = half; jc < p.W / 64; jc += 2) {
-    const uint2 mb = live ? *reinterpret_cast<const uint2 *>(mrow + 2 * jc) : make_uint2(0u, 0u);
-    const float4 *o4 = reinterpret_cast<const float4 *>(p.w_out + 64 * jc);
+    const uint2 mb = live ? ld_stream2(mrow + 2 * jc) : make_uint2(0u, 0u);
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
 #pragma unroll
     for (int c16 = 0; c16 < 8; ++c16) {
-      const float4 oa = __ldg(o4 + 2 * c16), ob = __ldg(o4 + 2 * c16 + 1);
+      const float4 oa = ld_keep(p.w_out + 64 * jc + 8 * c16);
+      const float4 ob = ld_keep(p.w_out + 64 * jc + 8 * c16 + 4);
       const float o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
-      const uint32_t m = (c16 < 4 ? mb.x : mb.y) >> ((8 * c16) & 31);
+      const uint32_t m = c16 < 4 ? mb.x : mb.y;
       uint32_t w[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e)
-        w[e] = pack2((m >> (2 * e)) & 1u ? dzr * o[2 * e] : 0.0f,
-                     (m >> (2 * e + 1)) & 1u ? dzr * o[2 * e + 1] : 0.0f);
+        w[e] = pack2(dzr * o[2 * e], dzr * o[2 * e + 1]) & pair_mask(m, (4 * c16 + e) & 15);
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
@@ -425,7 +475,7 @@ __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Sm
   uint2 mb[2] = {make_uint2(0u, 0u), make_uint2(0u, 0u)};
   if (live)  // before the wait: the ReLU bits of this warp's (at most two) chunks
     for (int k = 0; k < 2 && half + 2 * k < p.W / 64; ++k)
-      mb[k] = *reinterpret_cast<const uint2 *>(mrow + 2 * (half + 2 * k));
+      mb[k] = ld_stream2(mrow + 2 * (half + 2 * k));
   if (!warp_wait(&s.tfull[slot], tfull_phase & 1, p.err, 18)) return false;
   tc_fence_after();
   if (lane == 0) bulk_wait_read();
@@ -434,18 +484,17 @@ __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Sm
   uint8_t *A = s.A[slot];
   for (int k = 0, jc = half; jc < p.W / 64; ++k, jc += 2) {
     float v[64];
-    tmem_ld32(trow + 64 * jc, *reinterpret_cast<float(*)[32]>(v));
-    tmem_ld32(trow + 64 * jc + 32, *reinterpret_cast<float(*)[32]>(v + 32));
+    tmem_ld64(trow + 64 * jc, v);
     const uint2 m2 = k == 0 ? mb[0] : mb[1];
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
 #pragma unroll
     for (int c16 = 0; c16 < 8; ++c16) {
-      const uint32_t m = (c16 < 4 ? m2.x : m2.y) >> ((8 * c16) & 31);
+      const uint32_t m = c16 < 4 ? m2.x : m2.y;
       uint32_t w[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int i = 8 * c16 + 2 * e;
-        w[e] = pack2((m >> (2 * e)) & 1u ? v[i] : 0.0f, (m >> (2 * e + 1)) & 1u ? v[i + 1] : 0.0f);
+        w[e] = pack2(v[i], v[i + 1]) & pair_mask(m, (4 * c16 + e) & 15);
       }
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
