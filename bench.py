@@ -11,7 +11,10 @@ generation, encoding, MLP forward, forward model and loss, backward, Adam.
 Metric: training ray-samples per second (whole job over all ranks). A
 serving leg replays a seeded Poisson stream of mixed queries (time slices,
 sub-volumes, re-projections) against the query server of a cone-beam 6 x 256
-network and adds p50/p99 latency and outputs/s under "serving".
+network and adds p50/p99 latency and outputs/s under "serving". An
+equal-error leg trains the BF16 and FP32 paths for 200 steps from the same
+weights on the same minibatches and scores both reconstructions against the
+phantom ("equal_error").
 
 Our arm runs the library (default BF16 tensor-core path; the plain FP32 path
 is timed beside it). The reference arm (--impl reference) times the FP64 CPU
@@ -250,6 +253,11 @@ def run_ours(args):
         results[prec] = dict(dt=dt, steps=steps, prof=prof, clocks=ck.summary(), loss=loss,
                              e2e=ws * e2e_steps * B * S / e2e_dt)
         m.close()
+    if args.equal_error_steps > 0:
+        try:
+            results["equal_error"] = run_equal_error(args, w, proj, theta, rank)
+        except Exception as e:                       # reported, not hidden
+            results["equal_error"] = {"error": repr(e)}
     if args.serve_queries > 0:
         try:
             results["serving"] = run_serving(args, rank)
@@ -260,6 +268,48 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_equal_error(args, w, proj, theta, rank):
+    """Reconstruction error after the same number of Adam steps on both paths
+    (same initial weights, same minibatch indices): relative L2 error and
+    PSNR of mu0 M against the phantom's attenuation on a 64^3 grid inside the
+    field of view, at 8 view times."""
+    import torch
+
+    from paper_2404_19075_b300 import Dinr
+    from synthetic import truth, workloads as wl
+
+    g, net = w.geom, w.net
+    B, steps = w.train.batch_rays, args.equal_error_steps
+    ph = wl.phantom(w)
+    times = [(k + 0.5) / 8 for k in range(8)]
+    mask = truth.fov_mask(64)
+    gt = [truth.attenuation_grid(ph, t, 64) for t in times]
+    out = {"steps": steps, "grid": "64^3 cell centres inside the FOV cylinder",
+           "times": times, "batch_rays": B, "lr": w.train.lr}
+    for prec in ("bf16", "fp32"):
+        m = Dinr(g, net, w.train, proj, prec=prec, init_params=theta,
+                 sampler_seed=w.seeds["sampler"] + 1000 * rank)
+        losses = {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(1, steps + 1):
+            m.train_step(None, n=B, sync=False)
+            if k in (1, steps // 4, steps // 2, 3 * steps // 4, steps):
+                losses[k] = m.loss()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        sc = [truth.scores(m.query_grid(t, (-1, -1, -1), (1, 1, 1), (64, 64, 64)).cpu().numpy(),
+                           gt_t, mask) for t, gt_t in zip(times, gt)]
+        out[prec] = {"rel_l2": float(np.mean([x["rel_l2"] for x in sc])),
+                     "psnr_db": float(np.mean([x["psnr_db"] for x in sc])),
+                     "loss": losses, "wall_s": wall,
+                     "samples_per_s": steps * B * g.samples_per_ray / wall}
+        m.close()
+    out["bf16_over_fp32_rel_l2"] = out["bf16"]["rel_l2"] / out["fp32"]["rel_l2"]
+    out["equal_error"] = out["bf16_over_fp32_rel_l2"] <= 1.02
+    return out
 
 
 def run_serving(args, rank):
@@ -349,9 +399,10 @@ def emit(args, w, results, ws):
             "e2e": {"value": main["e2e"], "unit": "samples/s", "h2d_bytes_per_step": 8 * B,
                     "d2h_bytes_per_step": 4},
             "loss_last": main["loss"]}
-    serving = results.pop("serving", None)
-    if serving is not None:
-        line["serving"] = serving
+    for key in ("equal_error", "serving"):
+        extra = results.pop(key, None)
+        if extra is not None:
+            line[key] = extra
     for p, r in results.items():
         if p != args.prec:
             line[f"{p}_path"] = ({"error": r["error"]} if "error" in r else
@@ -374,6 +425,8 @@ def main():
     ap.add_argument("--rays", type=int, default=0,
                     help="rays per step (default: the workload's 65,536); smaller batches "
                          "are for profiler captures, not bench lines")
+    ap.add_argument("--equal-error-steps", type=int, default=200,
+                    help="Adam steps of the BF16-vs-FP32 reconstruction comparison (0 skips it)")
     ap.add_argument("--serve-queries", type=int, default=200,
                     help="queries of the serving leg (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
