@@ -54,8 +54,8 @@ def peaks():
 
 def config(w, extra=None):
     g, net = w.geom, w.net
-    c = {"workload": "parallel-beam 512 views x 128x128 detector, S=128, 10-octave encoding, "
-                     "MLP 5x256 ReLU, 65536 rays/step",
+    c = {"workload": ("parallel-beam 512 views x 128x128 detector, S=128, 10-octave encoding, "
+                      "MLP 5x256 ReLU, 65536 rays/step") if w.index == WORKLOAD else w.name,
          "rays_per_step": w.train.batch_rays, "samples_per_ray": g.samples_per_ray,
          "samples_per_step": w.train.batch_rays * g.samples_per_ray,
          "mlp": f"{net.hidden_layers}x{net.width}", "d_in": net.d_in,
@@ -153,7 +153,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    w = wl.workload(WORKLOAD)
+    w = wl.workload(args.workload)
     n_rays = 256
     for _ in range(args.warmup):
         oracle_rate(w, n_rays, seed=7)
@@ -201,7 +201,7 @@ def run_ours(args):
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    w = wl.workload(WORKLOAD)
+    w = wl.workload(args.workload)
     if args.rays:
         w = replace(w, train=replace(w.train, batch_rays=args.rays))
     g, net = w.geom, w.net
@@ -219,7 +219,7 @@ def run_ours(args):
     for prec in precs:
         try:
             m = Dinr(g, net, w.train, proj, prec=prec, init_params=theta,
-                     sampler_seed=w.seeds["sampler"] + 1000 * rank)
+                     sampler_seed=w.seeds["sampler"] + 1000 * rank, recompute=args.recompute)
         except DinrError as e:
             results[prec] = {"error": str(e)}
             continue
@@ -425,6 +425,11 @@ def main():
     ap.add_argument("--rays", type=int, default=0,
                     help="rays per step (default: the workload's 65,536); smaller batches "
                          "are for profiler captures, not bench lines")
+    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[2, 3, 4],
+                    help="training workload (default: the benchmark workload 2; 3 and 4 are "
+                         "the cone-beam 6x256 and 8x512 networks)")
+    ap.add_argument("--recompute", type=int, default=0,
+                    help="activation recomputation of the unfused BF16 path (0, 1, -1 auto)")
     ap.add_argument("--equal-error-steps", type=int, default=200,
                     help="Adam steps of the BF16-vs-FP32 reconstruction comparison (0 skips it)")
     ap.add_argument("--serve-queries", type=int, default=200,

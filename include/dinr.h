@@ -121,6 +121,17 @@ typedef struct {
   int chunk_rays;                /* rays processed per pass inside a step
                                     (bounds activation memory); 0 = automatic */
   uint64_t sampler_seed;
+  int recompute;                 /* activation recomputation of the BF16 path
+                                    without fused chains (W > 256): 0 keeps
+                                    every hidden output of a pass; 1 keeps
+                                    h_L for L % k == k - 1 (k = ceil(sqrt(H)))
+                                    and the last layer, and recomputes the
+                                    others in the backward with the same GEMM
+                                    (bitwise equal gradients, about 1/2 of a
+                                    forward more work, fewer activation bytes
+                                    per sample, so larger passes); negative:
+                                    on when a whole minibatch does not fit in
+                                    one pass without it. Ignored elsewhere. */
 } dinr_train;
 
 /* Number of FP32 parameters of a network shape (-1 for an invalid shape). */

@@ -45,7 +45,7 @@ class Train(C.Structure):
     _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
                 ("eps", C.c_double), ("lr_decay_per_epoch", C.c_double),
                 ("batch_rays", C.c_int), ("chunk_rays", C.c_int),
-                ("sampler_seed", C.c_uint64)]
+                ("sampler_seed", C.c_uint64), ("recompute", C.c_int)]
 
 
 class Request(C.Structure):

@@ -260,10 +260,15 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
   // workspace budget of 60 % of free memory, at most 96 GiB.
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
-  long long per_sample = workspace_bytes_per_sample(c);
   long long budget = (long long)(free_b * 0.6);
   if (budget > (96LL << 30)) budget = 96LL << 30;
-  long long max_rays = budget / (per_sample * c->S + 64);
+  c->recompute = 0;
+  long long max_rays = budget / (workspace_bytes_per_sample(c) * c->S + 64);
+  if (recompute_applies(c) &&
+      (train->recompute > 0 || (train->recompute < 0 && max_rays < c->batch_rays))) {
+    c->recompute = 1;
+    max_rays = budget / (workspace_bytes_per_sample(c) * c->S + 64);
+  }
   long long chunk = train->chunk_rays > 0 ? train->chunk_rays : c->batch_rays;
   if (chunk > c->batch_rays) chunk = c->batch_rays;
   if (chunk > max_rays) chunk = max_rays;

@@ -38,6 +38,7 @@ struct dinr_ctx {
 
   double lr = 1e-3, b1 = 0.9, b2 = 0.999, eps = 1e-8, decay = 1.0;
   int batch_rays = 0, chunk_rays = 0;
+  int recompute = 0;          // BF16 unfused path: keep checkpoints only (see dinr_train)
   uint64_t sampler_seed = 0;
   long long step = 0;  // completed Adam steps
 
@@ -81,6 +82,8 @@ struct ProfScope {
 // Pipeline (pipeline.cu)
 bool bf16_supported(const dinr_net *net);
 long long workspace_bytes_per_sample(const dinr_ctx *c);
+// Whether activation recomputation applies to this context's path.
+bool recompute_applies(const dinr_ctx *c);
 dinr_status alloc_workspace(dinr_ctx *c);
 void destroy_backend(dinr_ctx *c);
 // Loss into d_loss and gradient into d_grad for the n staged rays in d_idx.

@@ -27,6 +27,10 @@ static constexpr long long kMaxPartialFloats = 64LL << 20;
 
 bool bf16_supported(const dinr_net *net) { return tc_supported(net); }
 
+bool recompute_applies(const dinr_ctx *c) {
+  return c->prec == DINR_PREC_BF16 && tc_recompute_applies(c);
+}
+
 long long workspace_bytes_per_sample(const dinr_ctx *c) {
   if (c->prec == DINR_PREC_BF16) return tc_bytes_per_sample(c);
   return 4LL * (c->ldE + (long long)(c->H + 2) * c->W) + 8;

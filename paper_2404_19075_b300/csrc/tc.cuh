@@ -5,6 +5,7 @@
 
 bool tc_supported(const dinr_net *net);
 long long tc_bytes_per_sample(const dinr_ctx *c);
+bool tc_recompute_applies(const dinr_ctx *c);
 dinr_status tc_alloc(dinr_ctx *c);
 void tc_destroy(dinr_ctx *c);
 dinr_status tc_params_changed(dinr_ctx *c);

@@ -52,10 +52,15 @@ __device__ __forceinline__ int acc_stride(const TcGemmArgs &p) {
   return (cols + 31) / 32 * 32;
 }
 
-__device__ __forceinline__ void tile_range(const TcGemmArgs &p, int t, int &mt, int &sp,
+__device__ __forceinline__ int n_tn(const TcGemmArgs &p) { return p.n_tn > 1 ? p.n_tn : 1; }
+
+// Tile t -> M tile, N tile, K split and the K range of the split.
+__device__ __forceinline__ void tile_range(const TcGemmArgs &p, int t, int &mt, int &nt, int &sp,
                                            long long &k0, int &nk) {
   mt = t % p.m_tiles;
-  sp = t / p.m_tiles;
+  const int rest = t / p.m_tiles;
+  nt = rest % n_tn(p);
+  sp = rest / n_tn(p);
   k0 = (long long)sp * p.k_per_split;
   long long k1 = k0 + p.k_per_split < p.K ? k0 + p.k_per_split : p.K;
   nk = (int)((k1 - k0 + BK - 1) / BK);
@@ -74,11 +79,12 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
   const uint32_t nb_mn = (uint32_t)((p.N + 63) / 64);
   const uint32_t tx = (uint32_t)p.a_bytes + (uint32_t)p.b_bytes;
   uint32_t it = 0;
-  const int n_tiles = p.m_tiles * p.splits;
+  const int n_tiles = p.m_tiles * n_tn(p) * p.splits;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    int mt, sp, nk;
+    int mt, nt, sp, nk;
     long long k0;
-    tile_range(p, t, mt, sp, k0, nk);
+    tile_range(p, t, mt, nt, sp, k0, nk);
+    const int n0 = nt * p.N;
     for (int kb = 0; kb < nk; ++kb, ++it) {
       uint32_t st = it % S, rd = it / S;
       if (!mbar_wait(&s.empty[st], (rd & 1) ^ 1, p.err, 1)) return;
@@ -93,9 +99,10 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
         tma_load_2d(ta, &s.full[st], da + 8192, mt * BM + 64, kx);
       }
       if (!p.b_mn) {
-        tma_load_2d(tb, &s.full[st], db, kx, 0);
+        tma_load_2d(tb, &s.full[st], db, kx, n0);
       } else {
-        for (uint32_t j = 0; j < nb_mn; ++j) tma_load_2d(tb, &s.full[st], db + 8192 * j, 64 * j, kx);
+        for (uint32_t j = 0; j < nb_mn; ++j)
+          tma_load_2d(tb, &s.full[st], db + 8192 * j, n0 + 64 * (int)j, kx);
       }
     }
   }
@@ -115,12 +122,13 @@ __device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
   // an all-ones 16 x 16 BF16 block, no swizzle: every layout reads ones
   const uint64_t ones = smem_desc(smem_u32(s.ones), 128, 256, 0);
   uint32_t it = 0, lt = 0;
-  const int n_tiles = p.m_tiles * p.splits;
+  const int n_tiles = p.m_tiles * n_tn(p) * p.splits;
   bool ok = true;
   for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++lt) {
-    int mt, sp, nk;
+    int mt, nt, sp, nk;
     long long k0;
-    tile_range(p, t, mt, sp, k0, nk);
+    tile_range(p, t, mt, nt, sp, k0, nk);
+    const bool db_tile = p.with_db && nt == 0;
     uint32_t ab = lt % n_acc, ar = lt / n_acc;
     if (!mbar_wait(&s.tempty[ab], (ar & 1) ^ 1, p.err, 2)) break;
     tc_fence_after();
@@ -144,7 +152,7 @@ __device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
                                 : smem_desc(ba + 32 * k, 16, 1024, kSwizzle128);
         uint32_t acc = (kb | k) != 0;
         mma_bf16(d, adesc, bdesc, idesc, acc);
-        if (p.with_db) mma_bf16(d + p.N, adesc, ones, idesc_db, acc);
+        if (db_tile) mma_bf16(d + p.N, adesc, ones, idesc_db, acc);
       }
       mma_commit(&s.empty[st]);
     }
@@ -168,13 +176,14 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
   const int q = warp & 3;              // TMEM lane quadrant this warp may access
   const int half = (warp - 2) / 4;     // which alternate 32-column chunks
   const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
-  const int n_tiles = p.m_tiles * p.splits;
+  const int n_tiles = p.m_tiles * n_tn(p) * p.splits;
   const int n_chunks = (p.N + 31) / 32;
   uint32_t lt = 0;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
-    int mt, sp, nk;
+    int mt, nt, sp, nk;
     long long k0;
-    tile_range(p, t, mt, sp, k0, nk);
+    tile_range(p, t, mt, nt, sp, k0, nk);
+    const int n0 = nt * p.N;
     uint32_t ab = lt % n_acc, ar = lt / n_acc;
     const int r_in = q * 32 + lane;
     const int row = mt * BM + r_in;
@@ -182,17 +191,17 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
     // prefetch the mask operand of this warp's first chunk
     uint4 hcur[4], hnext[4];
     if (p.epi == kTcDx && live && half < n_chunks)
-      load_h32(p.hprev + (long long)row * p.ldh + half * 32, hcur);
+      load_h32(p.hprev + (long long)row * p.ldh + n0 + half * 32, hcur);
     if (!warp_wait(&s.tfull[ab], ar & 1, p.err, 5)) return;
     tc_fence_after();
     const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)acc_stride(p);
     float dot = 0.0f;
     for (int ch = half; ch < n_chunks; ch += 2) {
-      const int c0 = ch * 32;
+      const int c0 = n0 + ch * 32;  // output column of the chunk
       if (p.epi == kTcDx && live && ch + 2 < n_chunks)
         load_h32(p.hprev + (long long)row * p.ldh + c0 + 64, hnext);
       float v[32];
-      tmem_ld32(trow + c0, v);
+      tmem_ld32(trow + ch * 32, v);
       if (live) {
         if (p.epi == kTcFwd) {
 #pragma unroll
@@ -236,7 +245,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
         for (int j = 0; j < 4; ++j) hcur[j] = hnext[j];
       }
     }
-    if (p.epi == kTcDw && p.with_db && half == 0) {
+    if (p.epi == kTcDw && p.with_db && nt == 0 && half == 0) {
       float v[32];
       tmem_ld32(trow + p.N, v);  // 16 db columns (all equal) + padding
       if (live) p.part_db[(long long)sp * p.M + row] = v[0];
@@ -250,7 +259,12 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
         if (lane == 0) mbar_arrive(&s.dotbar[ab]);
       } else {
         if (!warp_wait(&s.dotbar[ab], ar & 1, p.err, 7)) return;
-        if (live) p.z_out[row] = dot + db[r_in] + p.b_out[0];
+        if (live) {
+          if (n_tn(p) > 1)
+            p.z_out[(long long)nt * p.M + row] = dot + db[r_in];
+          else
+            p.z_out[row] = dot + db[r_in] + p.b_out[0];
+        }
       }
     }
     tc_fence_before();
@@ -351,7 +365,7 @@ int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, TcGemmArgs a, i
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return (int)e;
-  int tiles = a.m_tiles * a.splits;
+  int tiles = a.m_tiles * (a.n_tn > 1 ? a.n_tn : 1) * a.splits;
   int grid = tiles < num_sms ? tiles : num_sms;
   k_tc_gemm<<<grid, kThreads, smem, st>>>(ta, tb, a);
   return (int)cudaGetLastError();

@@ -5,8 +5,9 @@
 //   A K-major: A(m, k) = A[m][k] (rows of samples), tile 128 x 64
 //   A MN-major: A(m, k) = A[k][m] (e.g. delta^T for weight gradients)
 //   B K-major: B(n, k) = B[n][k]; B MN-major: B(n, k) = B[k][n]
-// N <= 256 and a multiple of 16 (one N tile per CTA), M tiles of 128 rows,
-// K in blocks of 64 (TMA zero-fills past the tensor's extent).
+// N (the tile width) <= 256 and a multiple of 16; the output has n_tn tiles
+// of N columns (column offset nt * N), M tiles of 128 rows, K in blocks of
+// 64 (TMA zero-fills past the tensor's extent).
 #pragma once
 
 #include <cuda.h>
@@ -17,18 +18,20 @@ namespace dinr {
 
 enum TcEpi {
   kTcFwd = 0,  // out = bf16(act(acc + bias)); optional z_out = out . w_out + b_out
+               // (with n_tn > 1: z_out[nt][row] = the N-tile's part of out . w_out)
   kTcDx = 1,   // out = bf16(acc * [hprev > 0])
   kTcDw = 2    // part[split][m][n] = acc (FP32); optional part_db[split][m] = sum over k of A
 };
 
 struct TcGemmArgs {
   int epi;
-  int M, N;              // output rows / columns (MMA N)
+  int M, N;              // output rows / columns of one N tile (MMA N)
+  int n_tn;              // N tiles (0 or 1: one)
   long long K;           // reduction extent
   int a_mn, b_mn;
   int m_tiles, splits;
   long long k_per_split; // multiple of 64
-  int n_store;           // columns written (<= N)
+  int n_store;           // columns written (<= N * n_tn)
   // kTcFwd
   const float *bias;
   __nv_bfloat16 *out;

@@ -6,6 +6,10 @@
 // from the last: split-K weight-gradient GEMM (bias gradient from an
 // all-ones MMA in the same kernel) and the input-gradient GEMM with the ReLU
 // mask fused. Master weights, gradients, segment sums and loss stay FP32.
+// Widths up to 256 run the fused chains (tc_chain.cu) for the forward and
+// the input gradients; wider layers run as N-tiled GEMMs, optionally with
+// activation recomputation (only checkpoint layers kept, the others
+// recomputed by the same forward GEMM in the backward).
 #include "tc.cuh"
 #include "tc_chain.cuh"
 #include "tc_gemm.cuh"
@@ -42,6 +46,8 @@ struct TcState {
   float *rec = nullptr;           // per-ray records [samples][8] (chain path)
   float *ones = nullptr;          // 1.0 [samples], allocated when serving starts
   bool chain = false;
+  float *zpart = nullptr;         // [N tiles][samples] partial output dots (W > 256)
+  std::vector<int> owner;         // layer whose output each activation buffer holds
   float *zout = nullptr, *dz = nullptr, *ray_l = nullptr, *ray_p = nullptr, *pbar = nullptr,
         *sq = nullptr, *part = nullptr, *part_db = nullptr;
   long long part_floats = 0;
@@ -72,6 +78,16 @@ __global__ void k_out_delta_bf16(const float *dz, const float *w_out, const __nv
   int col = (int)(q - s * W);
   float x = __bfloat162float(h[q]);
   D[q] = __float2bfloat16_rn(x > 0.0f ? dz[s] * w_out[col] : 0.0f);
+}
+
+// z_out[s] = b_out + sum over N tiles of the partial dots, in tile order.
+__global__ void k_sum_parts(const float *part, int n_parts, long long n, const float *b_out,
+                            float *z_out) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  float z = part[s];
+  for (int k = 1; k < n_parts; ++k) z += part[(long long)k * n + s];
+  z_out[s] = z + b_out[0];
 }
 
 // part[z][c] = sum over rows of split z of w[s] * X[s][c] for BF16 X with C
@@ -150,18 +166,56 @@ dinr_status gemm(dinr_ctx *c, const char *name, double flops, double bytes, TcGe
   return DINR_OK;
 }
 
+// N tiles of a W-wide output: one tile up to 256 columns, else 256-wide tiles.
+int tile_w(int W) { return W <= 256 ? W : 256; }
+int tiles_n(int W) { return W <= 256 ? 1 : W / 256; }
+
+// Activation buffers of the unfused path. Without recomputation layer L has
+// buffer L. With it, h_L is kept only for checkpoint layers (L % k == k - 1
+// and the last layer, k = ceil(sqrt(H))); the other layers share k - 1
+// segment buffers (layer L uses L % k) and are recomputed when the backward
+// needs them. Consecutive layers never share a buffer.
+int rc_k(const dinr_ctx *c) {
+  int k = 1;
+  while (k * k < c->H) ++k;
+  return k;
+}
+bool is_ckpt(const dinr_ctx *c, int L) {
+  if (!c->recompute) return true;
+  const int k = rc_k(c);
+  return L == c->H - 1 || L % k == k - 1;
+}
+int n_ckpt(const dinr_ctx *c) {
+  int n = 0;
+  for (int L = 0; L < c->H; ++L) n += is_ckpt(c, L);
+  return n;
+}
+int h_slot(const dinr_ctx *c, int L) {
+  if (!c->recompute) return L;
+  if (is_ckpt(c, L)) {
+    int n = 0;
+    for (int j = 0; j < L; ++j) n += is_ckpt(c, j);
+    return n;
+  }
+  return n_ckpt(c) + L % rc_k(c);
+}
+int n_hbuf(const dinr_ctx *c) { return c->recompute ? n_ckpt(c) + rc_k(c) - 1 : c->H; }
+
 __nv_bfloat16 *hid(dinr_ctx *c, int L, long long ns) {
-  return S_(c)->H + (long long)L * ns * c->W;
+  return S_(c)->H + (long long)h_slot(c, L) * ns * c->W;
 }
 
-// Forward chain over ns samples whose features are in E.
-dinr_status forward(dinr_ctx *c, long long ns) {
+// Forward GEMMs of layers [L0, L1) over ns samples whose features are in E
+// (the last layer also forms z_out).
+dinr_status forward_layers(dinr_ctx *c, long long ns, int L0, int L1) {
   TcState *t = S_(c);
-  for (int L = 0; L < c->H; ++L) {
+  for (int L = L0; L < L1; ++L) {
+    const bool last = L == c->H - 1;
     TcGemmArgs a{};
     a.epi = kTcFwd;
     a.M = (int)ns;
-    a.N = c->W;
+    a.N = tile_w(c->W);
+    a.n_tn = tiles_n(c->W);
     a.K = t->kpad[L];
     a.m_tiles = (int)((ns + 127) / 128);
     a.splits = 1;
@@ -170,18 +224,36 @@ dinr_status forward(dinr_ctx *c, long long ns) {
     a.bias = c->d_params + c->offb[L];
     a.out = hid(c, L, ns);
     a.ldo = c->W;
-    if (L == c->H - 1) {
+    if (last) {
       a.w_out = c->d_params + c->offW[c->H];
       a.b_out = c->d_params + c->offb[c->H];
-      a.z_out = t->zout;
+      a.z_out = a.n_tn > 1 ? t->zpart : t->zout;
     }
     const void *A = L == 0 ? (const void *)t->E : (const void *)hid(c, L - 1, ns);
     long long acols = L == 0 ? c->ldE : c->W;
-    dinr_status s = gemm(c, "tc_fwd", 2.0 * ns * c->W * c->fan_in[L],
-                         2.0 * ns * (acols + c->W), a, A, ns, acols, t->Wb[L], c->W, t->kpad[L]);
+    dinr_status s = gemm(c, L0 > 0 || L1 < c->H ? "tc_fwd_recompute" : "tc_fwd",
+                         2.0 * ns * c->W * c->fan_in[L], 2.0 * ns * (acols + c->W), a, A, ns,
+                         acols, t->Wb[L], c->W, t->kpad[L]);
     if (s != DINR_OK) return s;
+    t->owner[h_slot(c, L)] = L;
+    if (last && a.n_tn > 1) {
+      k_sum_parts<<<ceil_div(ns, 256), 256, 0, c->st>>>(t->zpart, a.n_tn, ns, a.b_out, t->zout);
+      CKL();
+    }
   }
   return DINR_OK;
+}
+
+dinr_status forward(dinr_ctx *c, long long ns) { return forward_layers(c, ns, 0, c->H); }
+
+// Makes h_L available: recomputes the segment from the checkpoint below it
+// (or from E) when its buffer holds another layer.
+dinr_status ensure_hidden(dinr_ctx *c, long long ns, int L) {
+  TcState *t = S_(c);
+  if (t->owner[h_slot(c, L)] == L) return DINR_OK;
+  int c0 = L - 1;
+  while (c0 >= 0 && !is_ckpt(c, c0)) --c0;
+  return forward_layers(c, ns, c0 + 1, L + 1);
 }
 
 int chain_k0(const dinr_ctx *c) { return (c->d_in + 63) / 64 * 64; }
@@ -321,18 +393,23 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
   __nv_bfloat16 *Dn = t->D1;
   for (int L = c->H - 1; L >= 0; --L) {
     if (t->chain) D = t->Dall + (long long)L * ns * W;
+    if (L > 0 && !t->chain) {
+      s = ensure_hidden(c, ns, L - 1);
+      if (s != DINR_OK) return s;
+    }
     const void *In = L == 0 ? (const void *)t->E : (const void *)hid(c, L - 1, ns);
     int in_cols = L == 0 ? c->ldE : W;
     int fan_in = c->fan_in[L];
     TcGemmArgs a{};
     a.epi = kTcDw;
     a.M = W;
-    a.N = in_cols;
+    a.N = tile_w(in_cols);
+    a.n_tn = tiles_n(in_cols);
     a.K = ns;
     a.a_mn = 1;
     a.b_mn = 1;
     a.m_tiles = (W + 127) / 128;
-    a.splits = splits_for(ns, a.m_tiles, t->num_sms);
+    a.splits = splits_for(ns, a.m_tiles * a.n_tn, t->num_sms);
     a.k_per_split = ((ns + a.splits - 1) / a.splits + 63) / 64 * 64;
     a.splits = (int)((ns + a.k_per_split - 1) / a.k_per_split);
     a.n_store = fan_in;
@@ -351,7 +428,8 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
       TcGemmArgs b{};
       b.epi = kTcDx;
       b.M = (int)ns;
-      b.N = W;
+      b.N = tile_w(W);
+      b.n_tn = tiles_n(W);
       b.K = W;
       b.m_tiles = (int)((ns + 127) / 128);
       b.splits = 1;
@@ -388,19 +466,25 @@ dinr_status check_err(dinr_ctx *c) {
 static bool chains_used(const dinr_ctx *c);
 
 bool tc_supported(const dinr_net *net) {
-  // ReLU hidden layers; widths in [32, 256], multiples of 32 (one N tile,
-  // whole 32-column TMEM loads); at most 16 octaves (<= 144 padded inputs).
-  return net->act == DINR_ACT_RELU && net->width % 32 == 0 && net->width >= 32 &&
-         net->width <= 256 && net->n_freq <= 16;
+  // ReLU hidden layers; widths in [32, 256] in multiples of 32 (one N tile,
+  // whole 32-column TMEM loads) or 512, 768, 1024 (256-wide N tiles); at
+  // most 16 octaves (<= 144 padded inputs, one N tile of the first layer's
+  // weight gradient).
+  const int W = net->width;
+  return net->act == DINR_ACT_RELU && W % 32 == 0 && W >= 32 &&
+         (W <= 256 || (W % 256 == 0 && W <= 1024)) && net->n_freq <= 16;
 }
+
+static bool chains_used(const dinr_ctx *c) { return chain_ok(c) && c->H >= 2; }
+
+bool tc_recompute_applies(const dinr_ctx *c) { return !chains_used(c); }
 
 long long tc_bytes_per_sample(const dinr_ctx *c) {
   if (chains_used(c))
     return 2LL * (c->ldE + 2LL * c->H * c->W) + (long long)c->H * c->W / 8 + 32 + 8 + 16;
-  return 2LL * (c->ldE + (long long)(c->H + 2) * c->W) + 8 + 16;
+  return 2LL * (c->ldE + (long long)(n_hbuf(c) + 2) * c->W) + 8 + 16 +
+         (tiles_n(c->W) > 1 ? 4LL * tiles_n(c->W) : 0);
 }
-
-static bool chains_used(const dinr_ctx *c) { return chain_ok(c) && c->H >= 2; }
 
 dinr_status tc_alloc(dinr_ctx *c) {
   TcState *t = new TcState();
@@ -438,8 +522,10 @@ dinr_status tc_alloc(dinr_ctx *c) {
          grab((void **)&t->rec, 32ull * ns);
   else
     ok = ok && grab((void **)&t->D0, 2ull * ns * c->W) && grab((void **)&t->D1, 2ull * ns * c->W);
+  t->owner.assign(n_hbuf(c), -1);
+  if (tiles_n(c->W) > 1) ok = ok && grab((void **)&t->zpart, 4ull * ns * tiles_n(c->W));
   ok = ok && grab((void **)&t->E, 2ull * ns * c->ldE) &&
-       grab((void **)&t->H, 2ull * ns * c->W * c->H) && grab((void **)&t->zout, 4ull * ns) &&
+       grab((void **)&t->H, 2ull * ns * c->W * n_hbuf(c)) && grab((void **)&t->zout, 4ull * ns) &&
        grab((void **)&t->dz, 4ull * ns) && grab((void **)&t->ray_l, 4ull * ns) &&
        grab((void **)&t->ray_p, 4ull * ns) && grab((void **)&t->pbar, 4ull * ns) &&
        grab((void **)&t->sq, 4ull * ns) && grab((void **)&t->part, 4ull * t->part_floats) &&

@@ -67,7 +67,7 @@ class Dinr:
     """One DINR reconstruction on the current CUDA device."""
 
     def __init__(self, geometry, net, train, proj, prec="bf16", init_params=None,
-                 seed=0, sampler_seed=0, chunk_rays=0):
+                 seed=0, sampler_seed=0, chunk_rays=0, recompute=0):
         L = _abi.lib()
         self.geometry, self.net = geometry, net
         gs, self._keep = geometry_struct(geometry)
@@ -83,7 +83,7 @@ class Dinr:
                       seed)
         ts = _abi.Train(train.lr, train.beta1, train.beta2, train.eps,
                         getattr(train, "lr_decay_per_epoch", 1.0), train.batch_rays,
-                        chunk_rays, sampler_seed)
+                        chunk_rays, sampler_seed, recompute)
         self.stream = torch.cuda.current_stream()
         proj_t = _cuda_f32(proj)
         self.n_proj = geometry.n_views * geometry.det_rows * geometry.det_cols

@@ -49,7 +49,7 @@ def projections_for(w, idx):
 
 
 def make_model(w, prec, idx=None, proj=None, net=None, geom=None, batch=None, chunk=0,
-               params=None):
+               params=None, recompute=0):
     from paper_2404_19075_b300 import Dinr
     net = net or w.net
     geom = geom or w.geom
@@ -59,5 +59,5 @@ def make_model(w, prec, idx=None, proj=None, net=None, geom=None, batch=None, ch
         proj = projections_for(w, idx) if idx is not None else np.zeros(geom.n_proj, np.float32)
     train = wl.Train(batch or w.train.batch_rays)
     m = Dinr(geom, net, train, proj, prec=prec, init_params=params.astype(np.float32),
-             sampler_seed=w.seeds["sampler"], chunk_rays=chunk)
+             sampler_seed=w.seeds["sampler"], chunk_rays=chunk, recompute=recompute)
     return m, params.astype(np.float32).astype(np.float64), proj
