@@ -376,14 +376,18 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
     CKL();
   }
   int cs = colsum_splits(ns);
-  k_colsum_bf16<<<cs, 256, 0, c->st>>>(hH, W, ns, t->dz, cs, t->part);
-  CKL();
-  dinr_status s = reduce_into(c, t->part, cs, W, c->offW[c->H], acc);
-  if (s != DINR_OK) return s;
-  launch_colsum(t->dz, 1, 1, ns, nullptr, false, 0, cs, t->part, c->st);
-  CKL();
-  s = reduce_into(c, t->part, cs, 1, c->offb[c->H], acc);
-  if (s != DINR_OK) return s;
+  dinr_status s;
+  {
+    ProfScope ps(c, "dw_out", 2.0 * ns * W, 2.0 * ns * W + 4.0 * ns);
+    k_colsum_bf16<<<cs, 256, 0, c->st>>>(hH, W, ns, t->dz, cs, t->part);
+    CKL();
+    s = reduce_into(c, t->part, cs, W, c->offW[c->H], acc);
+    if (s != DINR_OK) return s;
+    launch_colsum(t->dz, 1, 1, ns, nullptr, false, 0, cs, t->part, c->st);
+    CKL();
+    s = reduce_into(c, t->part, cs, 1, c->offb[c->H], acc);
+    if (s != DINR_OK) return s;
+  }
 
   if (t->chain) {
     s = bwd_chain(c, ns);
