@@ -78,8 +78,16 @@ enum { DINR_OUT_IDENTITY = 0, DINR_OUT_SOFTPLUS = 1 };
 /* Arithmetic of the network GEMMs. Geometry, segment sums, loss and the
  * Adam master weights are FP32 (ray geometry FP64) in every mode.
  *   FP32: SIMT FP32 GEMMs, activations kept in HBM (the plain path).
- *   BF16: tcgen05 tensor-core GEMMs, BF16 operands, FP32 accumulation. */
-enum { DINR_PREC_FP32 = 0, DINR_PREC_BF16 = 1 };
+ *   BF16: tcgen05 tensor-core GEMMs, BF16 operands, FP32 accumulation.
+ *   FP8:  measured variant: the forward GEMMs take E4M3 operands with
+ *         per-tensor scales (weights: amax / 448 after every update;
+ *         features: 1; hidden outputs: delayed scaling, the amax of the
+ *         previous training step / 448, 1/32 before the first step;
+ *         forward-only calls use the current scales and do not update
+ *         them) and FP32 accumulation; the backward is the BF16 one, run on
+ *         the BF16 copies of the same activations. Unfused GEMMs only (no
+ *         fused chains, no recomputation, no query server). */
+enum { DINR_PREC_FP32 = 0, DINR_PREC_BF16 = 1, DINR_PREC_FP8 = 2 };
 
 typedef struct dinr_ctx dinr_ctx;
 

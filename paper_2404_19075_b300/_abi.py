@@ -21,7 +21,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_NONF
 BEAM = {"parallel": 0, "cone": 1}
 ACT = {"relu": 0, "swish": 1}
 OUT_ACT = {"identity": 0, "softplus": 1}
-PREC = {"fp32": 0, "bf16": 1}
+PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 
 
 class Geometry(C.Structure):

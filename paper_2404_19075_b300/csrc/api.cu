@@ -176,14 +176,14 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
       (net->act != DINR_ACT_RELU && net->act != DINR_ACT_SWISH) ||
       (net->out_act != DINR_OUT_IDENTITY && net->out_act != DINR_OUT_SOFTPLUS))
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid network shape");
-  if (net->prec != DINR_PREC_FP32 && net->prec != DINR_PREC_BF16)
+  if (net->prec != DINR_PREC_FP32 && net->prec != DINR_PREC_BF16 && net->prec != DINR_PREC_FP8)
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid precision");
   if (!train || train->batch_rays < 1 || train->chunk_rays < 0)
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid training options");
   if (!proj) return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "proj is NULL");
-  if (net->prec == DINR_PREC_BF16 && !bf16_supported(net))
+  if (net->prec != DINR_PREC_FP32 && !bf16_supported(net))
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_UNSUPPORTED,
-                                  "the BF16 path does not support this network shape");
+                                  "the tensor-core paths do not support this network shape");
 
   cudaGetLastError();  // a stale error of an earlier call is not this context's
   dinr_ctx *c = new (std::nothrow) dinr_ctx();

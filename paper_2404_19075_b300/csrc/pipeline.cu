@@ -28,11 +28,11 @@ static constexpr long long kMaxPartialFloats = 64LL << 20;
 bool bf16_supported(const dinr_net *net) { return tc_supported(net); }
 
 bool recompute_applies(const dinr_ctx *c) {
-  return c->prec == DINR_PREC_BF16 && tc_recompute_applies(c);
+  return c->prec != DINR_PREC_FP32 && tc_recompute_applies(c);
 }
 
 long long workspace_bytes_per_sample(const dinr_ctx *c) {
-  if (c->prec == DINR_PREC_BF16) return tc_bytes_per_sample(c);
+  if (c->prec != DINR_PREC_FP32) return tc_bytes_per_sample(c);
   return 4LL * (c->ldE + (long long)(c->H + 2) * c->W) + 8;
 }
 
@@ -47,7 +47,7 @@ static int dw_splits(long long rows, int M, int N) {
 }
 
 dinr_status alloc_workspace(dinr_ctx *c) {
-  if (c->prec == DINR_PREC_BF16) return tc_alloc(c);
+  if (c->prec != DINR_PREC_FP32) return tc_alloc(c);
   long long ns = (long long)c->chunk_rays * c->S;
   long long nr = ns;  // point queries use one "ray" per sample
   auto grab = [&](float **p, long long n) -> bool {
@@ -73,17 +73,17 @@ dinr_status alloc_workspace(dinr_ctx *c) {
 }
 
 void destroy_backend(dinr_ctx *c) {
-  if (c->prec == DINR_PREC_BF16) tc_destroy(c);
+  if (c->prec != DINR_PREC_FP32) tc_destroy(c);
 }
 
 dinr_status backend_poll(dinr_ctx *c) {
-  if (c->prec == DINR_PREC_BF16) return tc_poll(c);
+  if (c->prec != DINR_PREC_FP32) return tc_poll(c);
   CK(cudaStreamSynchronize(c->st));
   return DINR_OK;
 }
 
 dinr_status after_param_update(dinr_ctx *c) {
-  if (c->prec == DINR_PREC_BF16) return tc_params_changed(c);
+  if (c->prec != DINR_PREC_FP32) return tc_params_changed(c);
   return DINR_OK;
 }
 
@@ -260,17 +260,17 @@ static dinr_status f32_forward(dinr_ctx *c, const SourceArgs &src0, long long n_
 // ------------------------------------------------------------ dispatch
 
 dinr_status run_loss_grad(dinr_ctx *c, int n) {
-  if (c->prec == DINR_PREC_BF16) return tc_loss_grad(c, n);
+  if (c->prec != DINR_PREC_FP32) return tc_loss_grad(c, n);
   return f32_loss_grad(c, n);
 }
 
 dinr_status run_forward_rays(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S,
                              float *out) {
-  if (c->prec == DINR_PREC_BF16) return tc_forward_rays(c, src, n_rays, S, out);
+  if (c->prec != DINR_PREC_FP32) return tc_forward_rays(c, src, n_rays, S, out);
   return f32_forward(c, src, n_rays, S, out);
 }
 
 dinr_status run_forward_points(dinr_ctx *c, const SourceArgs &src, long long n, float *out) {
-  if (c->prec == DINR_PREC_BF16) return tc_forward_points(c, src, n, out);
+  if (c->prec != DINR_PREC_FP32) return tc_forward_points(c, src, n, out);
   return f32_forward(c, src, n, 1, out);
 }

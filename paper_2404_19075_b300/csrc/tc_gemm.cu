@@ -63,7 +63,16 @@ __device__ __forceinline__ void tile_range(const TcGemmArgs &p, int t, int &mt, 
   sp = rest / n_tn(p);
   k0 = (long long)sp * p.k_per_split;
   long long k1 = k0 + p.k_per_split < p.K ? k0 + p.k_per_split : p.K;
-  nk = (int)((k1 - k0 + BK - 1) / BK);
+  const int bk = p.fp8 ? 2 * BK : BK;  // K elements per 128-byte swizzled row
+  nk = (int)((k1 - k0 + bk - 1) / bk);
+}
+
+// Four E4M3 bytes (a in the lowest), round to nearest even, saturating.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+  uint16_t lo, hi;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+  return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -89,7 +98,7 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
       uint32_t st = it % S, rd = it / S;
       if (!mbar_wait(&s.empty[st], (rd & 1) ^ 1, p.err, 1)) return;
       mbar_expect_tx(&s.full[st], tx);
-      int kx = (int)(k0 + (long long)kb * BK);
+      int kx = (int)(k0 + (long long)kb * (p.fp8 ? 2 * BK : BK));
       uint8_t *da = s.a + (size_t)st * p.a_bytes;
       uint8_t *db = s.b + (size_t)st * p.b_bytes;
       if (!p.a_mn) {
@@ -117,7 +126,7 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
 __device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
   const int S = p.stages;
   const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
-  const uint32_t idesc = idesc_bf16(BM, p.N, p.a_mn, p.b_mn);
+  const uint32_t idesc = p.fp8 ? idesc_e4m3(BM, p.N) : idesc_bf16(BM, p.N, p.a_mn, p.b_mn);
   const uint32_t idesc_db = idesc_bf16(BM, 16, p.a_mn, false);
   // an all-ones 16 x 16 BF16 block, no swizzle: every layout reads ones
   const uint64_t ones = smem_desc(smem_u32(s.ones), 128, 256, 0);
@@ -151,7 +160,11 @@ __device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
         uint64_t bdesc = p.b_mn ? smem_desc(ba + 2048 * k, 8192, 1024, kSwizzle128)
                                 : smem_desc(ba + 32 * k, 16, 1024, kSwizzle128);
         uint32_t acc = (kb | k) != 0;
-        mma_bf16(d, adesc, bdesc, idesc, acc);
+        // both kinds take 32 bytes of K per instruction (16 BF16 or 32 E4M3)
+        if (p.fp8)
+          mma_fp8(d, adesc, bdesc, idesc, acc);
+        else
+          mma_bf16(d, adesc, bdesc, idesc, acc);
         if (db_tile) mma_bf16(d + p.N, adesc, ones, idesc_db, acc);
       }
       mma_commit(&s.empty[st]);
@@ -196,6 +209,9 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
     tc_fence_after();
     const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)acc_stride(p);
     float dot = 0.0f;
+    const float descale = p.fp8 ? *p.scale_a * *p.scale_b : 1.0f;
+    const float inv_out = p.out8 ? 1.0f / *p.scale_out : 0.0f;
+    float amax = 0.0f;
     for (int ch = half; ch < n_chunks; ch += 2) {
       const int c0 = n0 + ch * 32;  // output column of the chunk
       if (p.epi == kTcDx && live && ch + 2 < n_chunks)
@@ -207,9 +223,20 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             int c = c0 + i;
-            float x = fmaxf(v[i] + (c < p.n_store ? p.bias[c] : 0.0f), 0.0f);
+            float x = fmaxf(v[i] * descale + (c < p.n_store ? p.bias[c] : 0.0f), 0.0f);
             v[i] = x;
+            amax = fmaxf(amax, x);
             if (p.w_out && c < p.n_store) dot = fmaf(x, p.w_out[c], dot);
+          }
+          if (p.out8 && c0 + 32 <= p.n_store) {
+            uint32_t q8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) q8[j] = pack_e4m3x4(v[4 * j] * inv_out, v[4 * j + 1] * inv_out,
+                                                        v[4 * j + 2] * inv_out,
+                                                        v[4 * j + 3] * inv_out);
+            uint4 *o8 = reinterpret_cast<uint4 *>(p.out8 + (long long)row * p.ldo8 + c0);
+            o8[0] = make_uint4(q8[0], q8[1], q8[2], q8[3]);
+            o8[1] = make_uint4(q8[4], q8[5], q8[6], q8[7]);
           }
         } else if (p.epi == kTcDx) {
 #pragma unroll
@@ -244,6 +271,11 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) hcur[j] = hnext[j];
       }
+    }
+    if (p.amax) {
+      // activations are non-negative: their float bits order like integers
+      const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+      if (lane == 0 && m != 0u) atomicMax(p.amax, m);
     }
     if (p.epi == kTcDw && p.with_db && nt == 0 && half == 0) {
       float v[32];
@@ -352,8 +384,24 @@ bool make_tmap_bf16(CUtensorMap *tm, const void *ptr, long long rows, long long 
   return r == CUDA_SUCCESS;
 }
 
+bool make_tmap_u8(CUtensorMap *tm, const void *ptr, long long rows, long long cols, long long ld,
+                  int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld};
+  cuuint32_t box[2] = {128, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(ptr), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, TcGemmArgs a, int num_sms,
                    cudaStream_t st) {
+  if (a.fp8 && (a.epi != kTcFwd || a.a_mn || a.b_mn || a.with_db))
+    return (int)cudaErrorInvalidValue;
   a.a_bytes = BM * BK * 2;  // 128 rows x 128 bytes, or 2 MN-major boxes of 64 x 128 bytes
   a.b_bytes = a.b_mn ? ((a.N + 63) / 64) * 8192 : a.N * BK * 2;
   const int fixed = kOnesBytes + 2048 /*dot buffer*/ + 1024 /*alignment*/ + 256 /*barriers*/;

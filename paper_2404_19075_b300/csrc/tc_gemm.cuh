@@ -45,6 +45,15 @@ struct TcGemmArgs {
   float *part, *part_db;
   long long part_ld;
   int with_db;
+  // FP8 forward (kTcFwd only): E4M3 A and B, K-major, K blocks of 128; the
+  // accumulator is multiplied by *scale_a * *scale_b before the bias; when
+  // out8 is set the activations are also written as E4M3 of x / *scale_out
+  // (saturating), and the largest activation goes to *amax (float bits).
+  int fp8;
+  const float *scale_a, *scale_b, *scale_out;
+  uint8_t *out8;
+  long long ldo8;
+  unsigned int *amax;
   // launch geometry (filled by the launcher)
   int stages, a_bytes, b_bytes;
   int *err;              // device flag: nonzero when a bounded wait gave up
@@ -54,6 +63,9 @@ struct TcGemmArgs {
 // ld (elements), box {64, box_rows}, 128-byte swizzle, zero fill.
 bool make_tmap_bf16(CUtensorMap *tm, const void *ptr, long long rows, long long cols,
                     long long ld, int box_rows);
+// The same for a byte-element (E4M3) array, box {128, box_rows}.
+bool make_tmap_u8(CUtensorMap *tm, const void *ptr, long long rows, long long cols, long long ld,
+                  int box_rows);
 
 // Launches over min(tiles, SMs) persistent CTAs. Returns a cudaError_t.
 int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, TcGemmArgs a, int num_sms,

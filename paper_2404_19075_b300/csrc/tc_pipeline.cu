@@ -47,6 +47,14 @@ struct TcState {
   float *ones = nullptr;          // 1.0 [samples], allocated when serving starts
   bool chain = false;
   float *zpart = nullptr;         // [N tiles][samples] partial output dots (W > 256)
+  // FP8 forward (DINR_PREC_FP8): E4M3 copies of the features, of two
+  // consecutive hidden outputs and of the weights, and per-tensor scales
+  // fscale = [1 (features), s_w[H], s_h[H]] with amax records.
+  bool fp8 = false;
+  uint8_t *E8 = nullptr, *H8[2] = {nullptr, nullptr};
+  std::vector<uint8_t *> W8;
+  float *fscale = nullptr;
+  unsigned int *amax_w = nullptr, *amax_h = nullptr;
   std::vector<int> owner;         // layer whose output each activation buffer holds
   float *zout = nullptr, *dz = nullptr, *ray_l = nullptr, *ray_p = nullptr, *pbar = nullptr,
         *sq = nullptr, *part = nullptr, *part_db = nullptr;
@@ -78,6 +86,60 @@ __global__ void k_out_delta_bf16(const float *dz, const float *w_out, const __nv
   int col = (int)(q - s * W);
   float x = __bfloat162float(h[q]);
   D[q] = __float2bfloat16_rn(x > 0.0f ? dz[s] * w_out[col] : 0.0f);
+}
+
+// ---------------------------------------------------------------- FP8 (E4M3)
+// Per-tensor scaling: a tensor x is stored as e4m3(x / s) with s = amax / 448
+// (448 = the largest finite E4M3 value), so its largest magnitude lands on
+// the top of the format's range.
+constexpr float kE4M3Max = 448.0f;
+
+__device__ __forceinline__ uint16_t e4m3x2(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// *out = max |x| (as float bits; non-negative floats order like integers).
+__global__ void k_amax_abs(const float *x, long long n, unsigned int *out) {
+  float m = 0.0f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(x[i]));
+  const unsigned int b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+  if ((threadIdx.x & 31) == 0 && b != 0u) atomicMax(out, b);
+}
+
+// Wq[r][k] = e4m3(W[r][k] / s), zero for k >= cols, s = amax / 448 (1 if 0).
+__global__ void k_to_e4m3(const float *W, int rows, int cols, int kpad, const unsigned int *amax,
+                          float *scale, uint8_t *Wq) {
+  const float a = __uint_as_float(*amax);
+  const float s = a > 0.0f ? a / kE4M3Max : 1.0f;
+  long long q = 2 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  if (q == 0) *scale = s;
+  if (q >= (long long)rows * kpad) return;
+  int r = (int)(q / kpad), k = (int)(q - (long long)r * kpad);  // kpad is even
+  float x0 = k < cols ? W[(long long)r * cols + k] / s : 0.0f;
+  float x1 = k + 1 < cols ? W[(long long)r * cols + k + 1] / s : 0.0f;
+  *reinterpret_cast<uint16_t *>(Wq + q) = e4m3x2(x0, x1);
+}
+
+// E4M3 copy of BF16 features (scale 1: features lie in [-1, 1]).
+__global__ void k_bf16_to_e4m3(const __nv_bfloat16 *x, long long n, uint8_t *y) {
+  long long q = 2 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  if (q >= n) return;
+  *reinterpret_cast<uint16_t *>(y + q) =
+      e4m3x2(__bfloat162float(x[q]), q + 1 < n ? __bfloat162float(x[q + 1]) : 0.0f);
+}
+
+// Delayed scaling: the activation scales of the next step from this step's
+// amax records, which are then cleared.
+__global__ void k_fp8_scales(unsigned int *amax_h, float *s_h, int H) {
+  int L = threadIdx.x;
+  if (L >= H) return;
+  const float a = __uint_as_float(amax_h[L]);
+  if (a > 0.0f) s_h[L] = a / kE4M3Max;
+  amax_h[L] = 0u;
 }
 
 // z_out[s] = b_out + sum over N tiles of the partial dots, in tile order.
@@ -201,6 +263,24 @@ int h_slot(const dinr_ctx *c, int L) {
 }
 int n_hbuf(const dinr_ctx *c) { return c->recompute ? n_ckpt(c) + rc_k(c) - 1 : c->H; }
 
+// The FP8 forward GEMM of one layer (E4M3 A [ns][acols], B [W][K]).
+dinr_status gemm8(dinr_ctx *c, const char *name, double flops, double bytes, TcGemmArgs a,
+                  const void *A, long long a_rows, long long a_cols, const void *B,
+                  long long b_rows, long long b_cols) {
+  CUtensorMap ta, tb;
+  if (!make_tmap_u8(&ta, A, a_rows, a_cols, a_cols, 128) ||
+      !make_tmap_u8(&tb, B, b_rows, b_cols, b_cols, a.N))
+    return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "tensor map encoding failed (%s)", name);
+  a.err = S_(c)->err;
+  ProfScope ps(c, name, flops, bytes);
+  int e = launch_tc_gemm(ta, tb, a, S_(c)->num_sms, c->st);
+  ++c->launches;
+  if (e != 0)
+    return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "%s launch: %s", name,
+                                  cudaGetErrorString((cudaError_t)e));
+  return DINR_OK;
+}
+
 __nv_bfloat16 *hid(dinr_ctx *c, int L, long long ns) {
   return S_(c)->H + (long long)h_slot(c, L) * ns * c->W;
 }
@@ -209,6 +289,11 @@ __nv_bfloat16 *hid(dinr_ctx *c, int L, long long ns) {
 // (the last layer also forms z_out).
 dinr_status forward_layers(dinr_ctx *c, long long ns, int L0, int L1) {
   TcState *t = S_(c);
+  if (t->fp8 && L0 == 0) {
+    const long long n = ns * c->ldE;
+    k_bf16_to_e4m3<<<ceil_div((n + 1) / 2, 256), 256, 0, c->st>>>(t->E, n, t->E8);
+    CKL();
+  }
   for (int L = L0; L < L1; ++L) {
     const bool last = L == c->H - 1;
     TcGemmArgs a{};
@@ -229,11 +314,29 @@ dinr_status forward_layers(dinr_ctx *c, long long ns, int L0, int L1) {
       a.b_out = c->d_params + c->offb[c->H];
       a.z_out = a.n_tn > 1 ? t->zpart : t->zout;
     }
-    const void *A = L == 0 ? (const void *)t->E : (const void *)hid(c, L - 1, ns);
     long long acols = L == 0 ? c->ldE : c->W;
-    dinr_status s = gemm(c, L0 > 0 || L1 < c->H ? "tc_fwd_recompute" : "tc_fwd",
-                         2.0 * ns * c->W * c->fan_in[L], 2.0 * ns * (acols + c->W), a, A, ns,
-                         acols, t->Wb[L], c->W, t->kpad[L]);
+    dinr_status s;
+    if (t->fp8) {
+      const float *s_w = t->fscale + 1, *s_h = t->fscale + 1 + c->H;
+      a.fp8 = 1;
+      a.k_per_split = (a.K + 127) / 128 * 128;
+      a.scale_a = L == 0 ? t->fscale : s_h + (L - 1);
+      a.scale_b = s_w + L;
+      a.amax = t->amax_h + L;
+      if (!last) {
+        a.out8 = t->H8[L & 1];
+        a.ldo8 = c->W;
+        a.scale_out = s_h + L;
+      }
+      const void *A8 = L == 0 ? (const void *)t->E8 : (const void *)t->H8[(L - 1) & 1];
+      s = gemm8(c, "tc_fwd_fp8", 2.0 * ns * c->W * c->fan_in[L],
+                ns * (acols + 3.0 * c->W), a, A8, ns, acols, t->W8[L], c->W, t->kpad[L]);
+    } else {
+      const void *A = L == 0 ? (const void *)t->E : (const void *)hid(c, L - 1, ns);
+      s = gemm(c, L0 > 0 || L1 < c->H ? "tc_fwd_recompute" : "tc_fwd",
+               2.0 * ns * c->W * c->fan_in[L], 2.0 * ns * (acols + c->W), a, A, ns, acols,
+               t->Wb[L], c->W, t->kpad[L]);
+    }
     if (s != DINR_OK) return s;
     t->owner[h_slot(c, L)] = L;
     if (last && a.n_tn > 1) {
@@ -259,6 +362,7 @@ dinr_status ensure_hidden(dinr_ctx *c, long long ns, int L) {
 int chain_k0(const dinr_ctx *c) { return (c->d_in + 63) / 64 * 64; }
 
 bool chain_ok(const dinr_ctx *c) {
+  if (c->prec != DINR_PREC_BF16) return false;  // the chains compute in BF16
   if (!(c->W % 64 == 0 && c->W <= 256 && c->H <= kChainMaxLayers && chain_k0(c) <= 256 &&
         chain_supports_freq(c->F) && chain_stages(c->W, chain_k0(c)) >= 2))
     return false;
@@ -481,13 +585,16 @@ bool tc_supported(const dinr_net *net) {
 
 static bool chains_used(const dinr_ctx *c) { return chain_ok(c) && c->H >= 2; }
 
-bool tc_recompute_applies(const dinr_ctx *c) { return !chains_used(c); }
+bool tc_recompute_applies(const dinr_ctx *c) {
+  return !chains_used(c) && c->prec == DINR_PREC_BF16;
+}
 
 long long tc_bytes_per_sample(const dinr_ctx *c) {
   if (chains_used(c))
     return 2LL * (c->ldE + 2LL * c->H * c->W) + (long long)c->H * c->W / 8 + 32 + 8 + 16;
   return 2LL * (c->ldE + (long long)(n_hbuf(c) + 2) * c->W) + 8 + 16 +
-         (tiles_n(c->W) > 1 ? 4LL * tiles_n(c->W) : 0);
+         (tiles_n(c->W) > 1 ? 4LL * tiles_n(c->W) : 0) +
+         (c->prec == DINR_PREC_FP8 ? c->ldE + 2LL * c->W : 0);
 }
 
 dinr_status tc_alloc(dinr_ctx *c) {
@@ -527,6 +634,26 @@ dinr_status tc_alloc(dinr_ctx *c) {
   else
     ok = ok && grab((void **)&t->D0, 2ull * ns * c->W) && grab((void **)&t->D1, 2ull * ns * c->W);
   t->owner.assign(n_hbuf(c), -1);
+  t->fp8 = c->prec == DINR_PREC_FP8;
+  if (t->fp8) {
+    for (int L = 0; L < c->H; ++L) {
+      void *w8 = nullptr;
+      ok = ok && grab(&w8, (size_t)c->W * t->kpad[L]);
+      t->W8.push_back((uint8_t *)w8);
+    }
+    ok = ok && grab((void **)&t->E8, (size_t)ns * c->ldE) &&
+         grab((void **)&t->H8[0], (size_t)ns * c->W) && grab((void **)&t->H8[1], (size_t)ns * c->W) &&
+         grab((void **)&t->fscale, 4ull * (1 + 2 * c->H)) &&
+         grab((void **)&t->amax_w, 4ull * c->H) && grab((void **)&t->amax_h, 4ull * c->H);
+    if (ok) {
+      // features at scale 1; first-step activation scales 1/32 (values up to 14)
+      std::vector<float> f(1 + 2 * c->H, 1.0f);
+      for (int L = 0; L < c->H; ++L) f[1 + c->H + L] = 1.0f / 32.0f;
+      CK(cudaMemcpyAsync(t->fscale, f.data(), 4 * f.size(), cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemsetAsync(t->amax_h, 0, 4ull * c->H, c->st));
+      CK(cudaStreamSynchronize(c->st));
+    }
+  }
   if (tiles_n(c->W) > 1) ok = ok && grab((void **)&t->zpart, 4ull * ns * tiles_n(c->W));
   ok = ok && grab((void **)&t->E, 2ull * ns * c->ldE) &&
        grab((void **)&t->H, 2ull * ns * c->W * n_hbuf(c)) && grab((void **)&t->zout, 4ull * ns) &&
@@ -552,6 +679,15 @@ dinr_status tc_params_changed(dinr_ctx *c) {
     k_to_bf16<<<ceil_div((long long)rows * kp, 256), 256, 0, c->st>>>(
         c->d_params + c->offW[L], rows, cols, kp, t->Wb[L], t->WbT[L]);
     CKL();
+    if (t->fp8) {
+      CK(cudaMemsetAsync(t->amax_w + L, 0, 4, c->st));
+      k_amax_abs<<<148, 256, 0, c->st>>>(c->d_params + c->offW[L], (long long)rows * cols,
+                                         t->amax_w + L);
+      CKL();
+      k_to_e4m3<<<ceil_div((long long)rows * kp / 2, 256), 256, 0, c->st>>>(
+          c->d_params + c->offW[L], rows, cols, kp, t->amax_w + L, t->fscale + 1 + L, t->W8[L]);
+      CKL();
+    }
   }
   return DINR_OK;
 }
@@ -585,6 +721,10 @@ dinr_status tc_loss_grad(dinr_ctx *c, int n) {
     CKL();
     s = backward(c, ns, pass > 0);
     if (s != DINR_OK) return s;
+  }
+  if (t->fp8) {
+    k_fp8_scales<<<1, 32, 0, c->st>>>(t->amax_h, t->fscale + 1 + c->H, c->H);
+    CKL();
   }
   return DINR_OK;
 }
