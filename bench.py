@@ -162,6 +162,18 @@ def cpu_baseline(w, n_rays=2048):
                       f"FP64 step (numpy, BLAS threads = host cores), {dt:.1f} s"}
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -255,10 +267,7 @@ def run_ours(args):
             barrier()
         m.profile(False)
         prof = m.profile_report()
-        if ws > 1:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = t.item()
+        dt = max_over_ranks(dt)
         loss = m.loss()
         # end to end through the public API: host indices (pinned) in, loss out
         idx_host = torch.empty(B, dtype=torch.int64).pin_memory()
@@ -270,7 +279,7 @@ def run_ours(args):
             idx_host.numpy()[:] = rng.integers(0, g.n_proj, B)
             m.train_step_host(idx_host, sync=True)
         barrier()
-        e2e_dt = time.perf_counter() - t0
+        e2e_dt = max_over_ranks(time.perf_counter() - t0)
         results[prec] = dict(dt=dt, steps=steps, prof=prof, clocks=ck.summary(), loss=loss,
                              e2e=ws * e2e_steps * B * S / e2e_dt)
         m.close()
