@@ -462,9 +462,10 @@ def main():
     ap.add_argument("--rays", type=int, default=0,
                     help="rays per step (default: the workload's 65,536); smaller batches "
                          "are for profiler captures, not bench lines")
-    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[2, 3, 4],
+    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[2, 3, 4, 6],
                     help="training workload (default: the benchmark workload 2; 3 and 4 are "
-                         "the cone-beam 6x256 and 8x512 networks)")
+                         "the cone-beam 6x256 and 8x512 networks, 6 the paper's GRFF + Swish "
+                         "network on the geometry of 2)")
     ap.add_argument("--recompute", type=int, default=0,
                     help="activation recomputation of the unfused BF16 path (0, 1, -1 auto)")
     ap.add_argument("--equal-error-steps", type=int, default=200,

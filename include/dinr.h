@@ -31,10 +31,13 @@
  *   - The flat parameter vector (FP32) is laid out as
  *       [W_1 (width x d_in, row-major), b_1 (width),
  *        W_2 (width x width), b_2, ..., W_H, b_H, w_out (width), b_out (1)]
- *     with d_in = 4 + 8 * n_freq; its length is dinr_param_count().
- *   - Features of a normalised coordinate (t,z,y,x) are
- *       [t, z, y, x, then for c in (t,z,y,x), l = 0..F-1:
- *        sin(2^l pi c), cos(2^l pi c)].
+ *     with d_in = 4 + 8 * n_freq (octave encoding) or 2 * grff_c (GRFF);
+ *     its length is dinr_param_count() / dinr_param_count_din().
+ *   - Features of a normalised coordinate r = (t,z,y,x) are, with the octave
+ *     encoding, [t, z, y, x, then for c in (t,z,y,x), l = 0..F-1:
+ *     sin(2^l pi c), cos(2^l pi c)]; with the Gaussian random Fourier
+ *     features of App. B item 2, [cos(2 pi B r) (C values), sin(2 pi B r)
+ *     (C values)] for the frozen C x 4 matrix B.
  *   - Pixel centres: u = det_off_u + (col + 0.5) * det_pitch_u,
  *     v = det_off_v + (row + 0.5) * det_pitch_v; detector rows run along +z.
  *     At theta = 0 rays travel along +y and u runs along +x; the cone-beam
@@ -75,6 +78,7 @@ typedef enum {
 enum { DINR_BEAM_PARALLEL = 0, DINR_BEAM_CONE = 1 };
 enum { DINR_ACT_RELU = 0, DINR_ACT_SWISH = 1 };
 enum { DINR_OUT_IDENTITY = 0, DINR_OUT_SOFTPLUS = 1 };
+enum { DINR_ENC_OCTAVE = 0, DINR_ENC_GRFF = 1 };
 /* Arithmetic of the network GEMMs. Geometry, segment sums, loss and the
  * Adam master weights are FP32 (ray geometry FP64) in every mode.
  *   FP32: SIMT FP32 GEMMs, activations kept in HBM (the plain path).
@@ -119,6 +123,12 @@ typedef struct {
   const float *init_params;      /* host [dinr_param_count]; copied. NULL: He
                                     initialisation from `seed` */
   uint64_t seed;
+  int encoding;                  /* DINR_ENC_OCTAVE (n_freq used) or
+                                    DINR_ENC_GRFF (grff_c, grff_B used) */
+  int grff_c;                    /* C, even, 2..128 */
+  const float *grff_B;           /* host [grff_c][4], columns (t, z, y, x);
+                                    frozen; copied (App. B item 2: column t
+                                    ~ N(0, sigma_t^2), z y x ~ N(0, sigma_s^2)) */
 } dinr_net;
 
 /* Optimiser and minibatch (Sec. III, App. C). */
@@ -144,6 +154,9 @@ typedef struct {
 
 /* Number of FP32 parameters of a network shape (-1 for an invalid shape). */
 DINR_API int64_t dinr_param_count(int n_freq, int hidden_layers, int width);
+/* The same for any encoding width d_in (2 * grff_c for GRFF); -1 on bad
+ * arguments. */
+DINR_API int64_t dinr_param_count_din(int d_in, int hidden_layers, int width);
 
 /* Create a context: copies geometry, parameters and the measured projection
  * stack p[M*N] (FP32, index i = m*N + n, Sec. III) to the device, zeroes the

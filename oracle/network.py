@@ -40,6 +40,22 @@ def encode(rbar, n_freq: int):
     return np.concatenate(feats, axis=-1)
 
 
+def encode_grff(rbar, B):
+    """Gaussian random Fourier features (App. B item 2) of normalised
+    coordinates rbar [..., 4] with the frozen matrix B [C][4]:
+    [cos(2 pi B rbar), sin(2 pi B rbar)], the C cosines first. Returns
+    [..., 2C]."""
+    u = np.asarray(rbar, np.float64) @ np.asarray(B, np.float64).T
+    return np.concatenate([np.cos(2.0 * np.pi * u), np.sin(2.0 * np.pi * u)], axis=-1)
+
+
+def encode_net(rbar, net):
+    """The encoding the network uses (octave features or GRFF)."""
+    if getattr(net, "encoding", "octave") == "grff":
+        return encode_grff(rbar, net.grff_B)
+    return encode(rbar, net.n_freq)
+
+
 def layer_shapes(net):
     shapes = [(net.width, net.d_in)]
     shapes += [(net.width, net.width)] * (net.hidden_layers - 1)

@@ -26,7 +26,7 @@ def encoded_samples(geom, net, idx):
     o, d, s0, l, t = geometry.rays(geom, idx)
     P = geometry.sample_points(o, d, s0, l, geom.samples_per_ray)
     rbar = geometry.normalize(geom, P, t[:, None])
-    e = network.encode(rbar, net.n_freq)
+    e = network.encode_net(rbar, net)
     return e.reshape(-1, net.d_in), l
 
 
@@ -98,7 +98,7 @@ def project_view(theta, geom, net, view_theta, view_t, rows, cols, S):
     s0, l = geometry.fov_chord(geom, o, d)
     P = geometry.sample_points(o, d, s0, l, S)
     rbar = geometry.normalize(geom, P, view_t)
-    M, _ = network.forward(theta, net, network.encode(rbar, net.n_freq).reshape(-1, net.d_in))
+    M, _ = network.forward(theta, net, network.encode_net(rbar, net).reshape(-1, net.d_in))
     return forward_model(M.reshape(-1, S), l, S, geom.mu0).reshape(rows, cols)
 
 
@@ -108,7 +108,7 @@ def query(theta, geom, net, coords):
     coords = np.asarray(coords, np.float64)
     P = coords[:, [3, 2, 1]]
     rbar = geometry.normalize(geom, P, coords[:, 0])
-    M, _ = network.forward(theta, net, network.encode(rbar, net.n_freq))
+    M, _ = network.forward(theta, net, network.encode_net(rbar, net))
     return geom.mu0 * M
 
 

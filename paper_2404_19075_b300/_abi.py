@@ -22,6 +22,7 @@ BEAM = {"parallel": 0, "cone": 1}
 ACT = {"relu": 0, "swish": 1}
 OUT_ACT = {"identity": 0, "softplus": 1}
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
+ENCODING = {"octave": 0, "grff": 1}
 
 
 class Geometry(C.Structure):
@@ -38,7 +39,8 @@ class Geometry(C.Structure):
 class Net(C.Structure):
     _fields_ = [("n_freq", C.c_int), ("hidden_layers", C.c_int), ("width", C.c_int),
                 ("act", C.c_int), ("out_act", C.c_int), ("prec", C.c_int),
-                ("init_params", C.POINTER(C.c_float)), ("seed", C.c_uint64)]
+                ("init_params", C.POINTER(C.c_float)), ("seed", C.c_uint64),
+                ("encoding", C.c_int), ("grff_c", C.c_int), ("grff_B", C.POINTER(C.c_float))]
 
 
 class Train(C.Structure):
@@ -60,6 +62,7 @@ QUERY = {"points": 0, "grid": 1, "project": 2}
 vp, i64 = C.c_void_p, C.c_int64
 PROTOTYPES = {
     "dinr_param_count": (C.c_int64, [C.c_int, C.c_int, C.c_int]),
+    "dinr_param_count_din": (C.c_int64, [C.c_int, C.c_int, C.c_int]),
     "dinr_create": (C.c_int, [C.POINTER(Geometry), C.POINTER(Net), C.POINTER(Train), vp,
                               C.c_int, vp, C.POINTER(vp)]),
     "dinr_set_projections": (C.c_int, [vp, vp, C.c_int]),

@@ -48,10 +48,15 @@ int dinr_fail(dinr_ctx *c, int status, const char *fmt, ...) {
 
 // ------------------------------------------------------------ helpers
 
-int64_t dinr_param_count(int n_freq, int hidden_layers, int width) {
-  if (n_freq < 0 || hidden_layers < 1 || width < 1) return -1;
-  int64_t d_in = 4 + 8 * (int64_t)n_freq, W = width;
+int64_t dinr_param_count_din(int d_in, int hidden_layers, int width) {
+  if (d_in < 1 || hidden_layers < 1 || width < 1) return -1;
+  int64_t W = width;
   return W * d_in + W + (int64_t)(hidden_layers - 1) * (W * W + W) + W + 1;
+}
+
+int64_t dinr_param_count(int n_freq, int hidden_layers, int width) {
+  if (n_freq < 0) return -1;
+  return dinr_param_count_din(4 + 8 * n_freq, hidden_layers, width);
 }
 
 // He initialisation: SplitMix64 stream of `seed`, Box-Muller pairs (u1 from
@@ -176,6 +181,10 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
       (net->act != DINR_ACT_RELU && net->act != DINR_ACT_SWISH) ||
       (net->out_act != DINR_OUT_IDENTITY && net->out_act != DINR_OUT_SOFTPLUS))
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid network shape");
+  if (net->encoding != DINR_ENC_OCTAVE &&
+      (net->encoding != DINR_ENC_GRFF || net->grff_c < 2 || net->grff_c > kMaxGrff ||
+       net->grff_c % 2 != 0 || !net->grff_B))
+    return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid encoding");
   if (net->prec != DINR_PREC_FP32 && net->prec != DINR_PREC_BF16 && net->prec != DINR_PREC_FP8)
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid precision");
   if (!train || train->batch_rays < 1 || train->chunk_rays < 0)
@@ -197,6 +206,11 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
   c->out_act = net->out_act;
   c->prec = net->prec;
   c->d_in = 4 + 8 * c->F;
+  if (net->encoding == DINR_ENC_GRFF) {
+    c->grff_c = net->grff_c;
+    c->grff_B.assign(net->grff_B, net->grff_B + 4 * net->grff_c);
+    c->d_in = 2 * c->grff_c;
+  }
   c->ldE = (c->d_in + 15) / 16 * 16;
   c->S = geom->samples_per_ray;
   c->mu0 = (float)geom->mu0;
@@ -237,6 +251,7 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
   c->d_proj = (float *)dev_alloc(c, sizeof(float) * c->n_proj, &ok);
   c->d_idx = (long long *)dev_alloc(c, sizeof(long long) * c->batch_rays, &ok);
   c->d_flag = (int *)dev_alloc(c, sizeof(int) * 4, &ok);
+  if (c->grff_c > 0) c->d_grff_B = (float *)dev_alloc(c, sizeof(float) * 4 * c->grff_c, &ok);
   if (!ok) {
     dinr_fail(c, DINR_ERR_OOM, "device allocation of parameters/projections failed");
     return create_fail(c, DINR_ERR_OOM);
@@ -253,6 +268,9 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
   CK(cudaMemsetAsync(c->d_grad, 0, sizeof(float) * c->P, st));
   CK(cudaMemsetAsync(c->d_loss, 0, sizeof(float) * 4, st));
   CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int) * 4, st));
+  if (c->grff_c > 0)
+    CK(cudaMemcpyAsync(c->d_grff_B, c->grff_B.data(), sizeof(float) * 4 * c->grff_c,
+                       cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(c->d_proj, proj, sizeof(float) * c->n_proj,
                      proj_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
 

@@ -10,6 +10,7 @@
 namespace dinr {
 
 constexpr int kMaxFreq = 16;
+constexpr int kMaxGrff = 128;  // GRFF frequencies C (2C = 256 features)
 
 // Geometry as the kernels see it. Per-view angle cosines/sines and
 // normalised times are computed on the host in FP64 at creation.

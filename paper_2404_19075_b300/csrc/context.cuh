@@ -26,6 +26,9 @@ struct dinr_ctx {
 
   // network: layer L = 0..H-1 hidden, L = H output; offsets into the flat vector
   int F = 0, H = 0, W = 0, act = 0, out_act = 0, prec = 0, d_in = 0, ldE = 0;
+  int grff_c = 0;                  // GRFF encoding: C frequencies (0: octave encoding)
+  std::vector<float> grff_B;       // host copy [C][4]
+  float *d_grff_B = nullptr;       // device copy [C][4]
   long long P = 0;
   std::vector<int> fan_in, fan_out;
   std::vector<long long> offW, offb;

@@ -72,12 +72,14 @@ __device__ __forceinline__ void source_coords(const GeoDev &g, const SourceArgs 
 // Encoded features of a pass. Rays r in [0, n_rays) own samples
 // [r*S, r*S + S) (S = 1 for point sources). Features are written as
 // FP32 or BF16 [n_samples][ld] with zero padding from d_in to ld.
+// grff_c > 0 selects the Gaussian random Fourier features of the device
+// matrix grff_B [grff_c][4] in place of the octave features.
 void launch_encode_f32(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
-                       int F, int ld, float *E, float *ray_l, const float *proj,
-                       float *ray_p, cudaStream_t st);
+                       int F, int grff_c, const float *grff_B, int ld, float *E, float *ray_l,
+                       const float *proj, float *ray_p, cudaStream_t st);
 void launch_encode_bf16(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
-                        int F, int ld, __nv_bfloat16 *E, float *ray_l, const float *proj,
-                        float *ray_p, cudaStream_t st);
+                        int F, int grff_c, const float *grff_B, int ld, __nv_bfloat16 *E,
+                        float *ray_l, const float *proj, float *ray_p, cudaStream_t st);
 
 void launch_sample_indices(long long n_proj, int B, long long step, uint64_t seed,
                            long long *out, cudaStream_t st);

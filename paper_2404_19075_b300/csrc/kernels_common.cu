@@ -159,13 +159,45 @@ constexpr int kEncThreads = 128;
 // which are contiguous in E, with coalesced 32-bit stores. ray_l receives
 // each ray's chord length (1 for point sources, so that the forward model
 // reduces to mu0 * M); ray_p the measured value of each training ray.
+// Gaussian random Fourier features (App. B item 2) of one sample: for
+// frequency k, u = B[k] . r; cos(2 pi u) into column k, sin(2 pi u) into
+// column C + k. The phase is reduced exactly, 2u - 2 rint(u) in [-1, 1], then
+// sincospif; u is formed in FP64 for the FP32 path and in FP32 (error about
+// 1e-7 |u|, far below BF16 resolution) for the BF16 path.
+template <typename T, bool kFast>
+__device__ __forceinline__ void grff_row(uint32_t *row, const double (&c)[4], const float *B,
+                                         int C) {
+  for (int k = 0; k < C; k += 2) {
+    float sv[2], cv[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float *b = B + 4 * (k + e);
+      float y;
+      if (kFast) {
+        const float u = fmaf(b[0], (float)c[0],
+                             fmaf(b[1], (float)c[1], fmaf(b[2], (float)c[2], b[3] * (float)c[3])));
+        y = 2.0f * (u - rintf(u));
+      } else {
+        const double u = (double)b[0] * c[0] + (double)b[1] * c[1] + (double)b[2] * c[2] +
+                         (double)b[3] * c[3];
+        y = (float)(2.0 * (u - rint(u)));
+      }
+      sincospif(y, &sv[e], &cv[e]);
+    }
+    FeatWriter<T>::put(row, k, cv[0], cv[1]);
+    FeatWriter<T>::put(row, C + k, sv[0], sv[1]);
+  }
+}
+
 template <typename T, bool kFast>
 __global__ void __launch_bounds__(kEncThreads)
-    k_encode(GeoDev g, SourceArgs src, long long n_rays, int S, int F, int ld, T *E,
-             float *ray_l, const float *proj, float *ray_p) {
+    k_encode(GeoDev g, SourceArgs src, long long n_rays, int S, int F, int grff_c,
+             const float *grff_B, int ld, T *E, float *ray_l, const float *proj, float *ray_p) {
   extern __shared__ uint32_t enc_smem[];
   __shared__ Ray rays[kEncThreads];
   __shared__ float tfeat[kEncThreads][2 * kMaxFreq];
+  __shared__ float sB[4 * kMaxGrff];
+  for (int i = threadIdx.x; i < 4 * grff_c; i += blockDim.x) sB[i] = grff_B[i];
   const int words = ld * (int)sizeof(T) / 4;
   const int stride = words + 1;  // odd stride: conflict-free row writes
   const long long n = n_rays * S;
@@ -180,7 +212,7 @@ __global__ void __launch_bounds__(kEncThreads)
     long long r = r_first + tid;
     Ray ray = source_ray(g, src, r);
     rays[tid] = ray;
-    coord_features<kFast>(ray.tbar, F, tfeat[tid]);
+    if (grff_c == 0) coord_features<kFast>(ray.tbar, F, tfeat[tid]);
     if (r * S >= q0) {  // the block holding the ray's first sample reports it
       if (ray_l) ray_l[r] = (float)ray.l;
       if (ray_p) ray_p[r] = proj ? proj[src.idx[r]] : 0.0f;
@@ -199,13 +231,18 @@ __global__ void __launch_bounds__(kEncThreads)
       int k = (int)(r - r_first);
       c[0] = rays[k].tbar;
       sample_coords(g, rays[k], j, S, c[1], c[2], c[3]);
-      for (int l = 0; l < 2 * F; ++l) sc[l] = tfeat[k][l];
+      if (grff_c == 0)
+        for (int l = 0; l < 2 * F; ++l) sc[l] = tfeat[k][l];
     } else {
       float len;
       source_coords(g, src, r, j, S, c, &len);
       if (ray_l) ray_l[r] = 1.0f;
-      coord_features<kFast>(c[0], F, sc);
+      if (grff_c == 0) coord_features<kFast>(c[0], F, sc);
     }
+    if (grff_c > 0) {
+      grff_row<T, kFast>(row, c, sB, grff_c);
+      for (int f = 2 * grff_c; f < ld; f += 2) FeatWriter<T>::put(row, f, 0.0f, 0.0f);
+    } else {
     FeatWriter<T>::put(row, 0, (float)c[0], (float)c[1]);
     FeatWriter<T>::put(row, 2, (float)c[2], (float)c[3]);
     for (int l = 0; l < F; ++l) FeatWriter<T>::put(row, 4 + 2 * l, sc[2 * l], sc[2 * l + 1]);
@@ -215,6 +252,7 @@ __global__ void __launch_bounds__(kEncThreads)
         FeatWriter<T>::put(row, 4 + 2 * F * k + 2 * l, sc[2 * l], sc[2 * l + 1]);
     }
     for (int f = 4 + 8 * F; f < ld; f += 2) FeatWriter<T>::put(row, f, 0.0f, 0.0f);
+    }
   }
   __syncthreads();
 
@@ -228,31 +266,33 @@ __global__ void __launch_bounds__(kEncThreads)
 
 template <typename T, bool kFast>
 static void launch_encode(const GeoDev &g, const SourceArgs &src, long long n_rays, int S, int F,
-                          int ld, T *E, float *ray_l, const float *proj, float *ray_p,
-                          cudaStream_t st) {
+                          int grff_c, const float *grff_B, int ld, T *E, float *ray_l,
+                          const float *proj, float *ray_p, cudaStream_t st) {
   long long n = n_rays * S;
   int words = ld * (int)sizeof(T) / 4;
   size_t smem = (size_t)kEncThreads * (words + 1) * 4;
   static bool attr = false;
   if (!attr) {
+    // rows of up to 256 FP32 features (GRFF with C = 128): 128 x 257 words
     cudaFuncSetAttribute(k_encode<T, kFast>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         96 * 1024);
+                         160 * 1024);
     attr = true;
   }
-  k_encode<T, kFast><<<ceil_div(n, kEncThreads), kEncThreads, smem, st>>>(g, src, n_rays, S, F,
-                                                                         ld, E, ray_l, proj,
-                                                                         ray_p);
+  k_encode<T, kFast><<<ceil_div(n, kEncThreads), kEncThreads, smem, st>>>(
+      g, src, n_rays, S, F, grff_c, grff_B, ld, E, ray_l, proj, ray_p);
 }
 
 void launch_encode_f32(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
-                       int F, int ld, float *E, float *ray_l, const float *proj,
-                       float *ray_p, cudaStream_t st) {
-  launch_encode<float, false>(g, src, n_rays, S, F, ld, E, ray_l, proj, ray_p, st);
+                       int F, int grff_c, const float *grff_B, int ld, float *E, float *ray_l,
+                       const float *proj, float *ray_p, cudaStream_t st) {
+  launch_encode<float, false>(g, src, n_rays, S, F, grff_c, grff_B, ld, E, ray_l, proj, ray_p,
+                              st);
 }
 void launch_encode_bf16(const GeoDev &g, const SourceArgs &src, long long n_rays, int S,
-                        int F, int ld, __nv_bfloat16 *E, float *ray_l, const float *proj,
-                        float *ray_p, cudaStream_t st) {
-  launch_encode<__nv_bfloat16, true>(g, src, n_rays, S, F, ld, E, ray_l, proj, ray_p, st);
+                        int F, int grff_c, const float *grff_B, int ld, __nv_bfloat16 *E,
+                        float *ray_l, const float *proj, float *ray_p, cudaStream_t st) {
+  launch_encode<__nv_bfloat16, true>(g, src, n_rays, S, F, grff_c, grff_B, ld, E, ray_l, proj,
+                                     ray_p, st);
 }
 
 // ------------------------------------- output layer, forward model, loss

@@ -215,7 +215,36 @@ __device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
 // K-chunks this warp owns, in the 128B-swizzled layout the MMA reads.
 template <int F>
 __device__ __forceinline__ void write_features(uint8_t *A, const float (&c)[4], bool live,
-                                               int r_in, int half) {
+                                               int r_in, int half, const float (*B)[4]) {
+  if constexpr (F == kGrffChain) {
+    // GRFF (App. B item 2): frequencies 64 half .. 64 half + 63; cosines go
+    // to chunk `half` (columns k), sines to chunk `half + 2` (columns C + k).
+    // The phase u = B[k] . r is reduced to [-1/2, 1/2] turns, then one fast
+    // sincos (absolute error about 1e-6, far below BF16 resolution).
+    uint32_t wc[32], ws[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      float cv[2], sv[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float *b = B[64 * half + 2 * i + e];
+        const float u = fmaf(b[0], c[0], fmaf(b[1], c[1], fmaf(b[2], c[2], b[3] * c[3])));
+        __sincosf(6.28318530717958648f * (u - rintf(u)), &sv[e], &cv[e]);
+      }
+      wc[i] = live ? pack2(cv[0], cv[1]) : 0u;
+      ws[i] = live ? pack2(sv[0], sv[1]) : 0u;
+    }
+    uint8_t *chc = A + (size_t)half * kChunkBytes;
+    uint8_t *chs = A + (size_t)(half + 2) * kChunkBytes;
+#pragma unroll
+    for (int c16 = 0; c16 < 8; ++c16) {
+      *reinterpret_cast<uint4 *>(chc + swz(r_in, c16)) =
+          make_uint4(wc[4 * c16], wc[4 * c16 + 1], wc[4 * c16 + 2], wc[4 * c16 + 3]);
+      *reinterpret_cast<uint4 *>(chs + swz(r_in, c16)) =
+          make_uint4(ws[4 * c16], ws[4 * c16 + 1], ws[4 * c16 + 2], ws[4 * c16 + 3]);
+    }
+    return;
+  }
   constexpr int kDin = 4 + 8 * F;
   constexpr int kChunks = (kDin + 63) / 64;
 #pragma unroll
@@ -295,7 +324,7 @@ __device__ __forceinline__ void tile_features(const ChainArgs &p, uint8_t *A, lo
     for (int k = 0; k < 4; ++k) c[k] = (float)cd[k];
     if (half == 0 && p.ray_l) p.ray_l[smp] = 1.0f;
   }
-  write_features<F>(A, c, live, r_in, half);
+  write_features<F>(A, c, live, r_in, half, p.grff_B);
 }
 
 
@@ -336,14 +365,14 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
     } else {
       live = false;
     }
-    write_features<F>(A, c, live, r_in, half);
+    write_features<F>(A, c, live, r_in, half, p.grff_B);
   } else {
     tile_features<F>(p, A, tile, smp, live, r_in, q, half, lane);
   }
   fence_async_smem();
   __syncwarp();
   if (lane == 0 && p.store_h && tile * 128 + q * 32 < p.ns) {
-    for (int jc = half; jc < (4 + 8 * F + 63) / 64; jc += 2)
+    for (int jc = half; jc < (p.d_in + 63) / 64; jc += 2)
       tma_store_2d(&maps.e, A + (size_t)jc * kChunkBytes + q * 32 * 128, 64 * jc,
                    (int)(tile * 128 + q * 32));
     bulk_commit();
@@ -615,6 +644,7 @@ int chain_stages(int W, int k0) {
 }
 
 bool chain_supports_freq(int F) { return F == 6 || F == 8 || F == 10 || F == 12 || F == 16; }
+bool chain_supports_grff(int C) { return C == kGrffChain; }
 
 template <int F, bool kBwd>
 static int launch_f(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
@@ -628,6 +658,8 @@ static int launch_f(const ChainMaps &maps, const ChainArgs &a, int num_sms, cuda
 }
 
 int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
+  if (a.grff_c == kGrffChain) return launch_f<kGrffChain, false>(maps, a, num_sms, st);
+  if (a.grff_c != 0) return (int)cudaErrorInvalidValue;
   switch (a.F) {
     case 6: return launch_f<6, false>(maps, a, num_sms, st);
     case 8: return launch_f<8, false>(maps, a, num_sms, st);

@@ -10,6 +10,9 @@
 namespace dinr {
 
 constexpr int kChainMaxLayers = 8;
+// Template value of the encoding for Gaussian random Fourier features with
+// C = 128 (2C = 256 inputs); octave encodings use F itself (<= 16).
+constexpr int kGrffChain = 128;
 
 // One piece of a serving batch: samples [0, n) of a query, starting at tile
 // tile0 of the batch (items start on 128-sample tile boundaries).
@@ -35,6 +38,8 @@ struct ChainArgs {
   SourceArgs src;
   long long n_rays;
   int S, F, d_in;
+  int grff_c;                      // GRFF encoding (C = 128) or 0 (octave features)
+  float grff_B[kGrffChain][4];     // frozen GRFF matrix (t, z, y, x columns)
   int k0;                          // layer-0 K padded to a multiple of 64
   int W, H;
   long long ns;                    // samples = n_rays * S
@@ -70,6 +75,7 @@ void launch_ray_records(const GeoDev &g, const SourceArgs &src, long long n_rays
 size_t chain_smem_bytes(int W, int k0, int stages);
 int chain_stages(int W, int k0);
 bool chain_supports_freq(int F);
+bool chain_supports_grff(int C);
 int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st);
 // Backward chain (H >= 2): delta_{H-1} = dz w_out [h_{H-1} > 0], then
 // delta_{L-1} = (delta_L W_L) [h_{L-1} > 0] for L = H-1..1, all on chip, with

@@ -184,6 +184,12 @@ __device__ __forceinline__ void load_h32(const __nv_bfloat16 *p, uint4 (&h)[4]) 
 
 __device__ __forceinline__ bool bf16_positive(uint32_t b) { return b != 0 && (b & 0x8000u) == 0; }
 
+// d/dz of z sigmoid(z) = sigmoid(z) (1 + z (1 - sigmoid(z))).
+__device__ __forceinline__ float swish_grad(float z) {
+  const float s = __frcp_rn(1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
 __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int q = warp & 3;              // TMEM lane quadrant this warp may access
@@ -216,18 +222,46 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
       const int c0 = n0 + ch * 32;  // output column of the chunk
       if (p.epi == kTcDx && live && ch + 2 < n_chunks)
         load_h32(p.hprev + (long long)row * p.ldh + c0 + 64, hnext);
+      // forward: the chunk's bias first, so that its load overlaps the TMEM load
+      float4 bb[8];
+      if (p.epi == kTcFwd) {
+        const float4 *b4 = reinterpret_cast<const float4 *>(p.bias + c0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) bb[j] = c0 + 4 * j < p.n_store ? __ldg(b4 + j) : make_float4(0, 0, 0, 0);
+      }
       float v[32];
       tmem_ld32(trow + ch * 32, v);
       if (live) {
         if (p.epi == kTcFwd) {
+          // z = descale * acc + bias; x = act(z). Swish uses a fast
+          // exponential and reciprocal (relative error about 1e-6, far below
+          // the BF16 rounding of x).
+          float x[32];
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            int c = c0 + i;
-            float x = fmaxf(v[i] * descale + (c < p.n_store ? p.bias[c] : 0.0f), 0.0f);
-            v[i] = x;
-            amax = fmaxf(amax, x);
-            if (p.w_out && c < p.n_store) dot = fmaf(x, p.w_out[c], dot);
+            const float4 b = bb[i / 4];
+            const float bi = (i & 3) == 0 ? b.x : (i & 3) == 1 ? b.y : (i & 3) == 2 ? b.z : b.w;
+            const float z = fmaf(v[i], descale, bi);
+            x[i] = p.act ? z * __frcp_rn(1.0f + __expf(-z)) : fmaxf(z, 0.0f);
+            v[i] = z;
+            amax = fmaxf(amax, fabsf(x[i]));
           }
+          if (p.w_out) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < p.n_store) dot = fmaf(x[i], __ldg(p.w_out + c0 + i), dot);
+          }
+          if (p.zpre && c0 + 32 <= p.n_store) {
+            uint4 *oz = reinterpret_cast<uint4 *>(p.zpre + (long long)row * p.ldz + c0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              oz[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]),
+                                 pack_bf16(v[8 * j + 2], v[8 * j + 3]),
+                                 pack_bf16(v[8 * j + 4], v[8 * j + 5]),
+                                 pack_bf16(v[8 * j + 6], v[8 * j + 7]));
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = x[i];
           if (p.out8 && c0 + 32 <= p.n_store) {
             uint32_t q8[8];
 #pragma unroll
@@ -244,8 +278,13 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
             uint32_t w[4] = {hcur[j].x, hcur[j].y, hcur[j].z, hcur[j].w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              if (!bf16_positive(w[e] & 0xFFFFu)) v[8 * j + 2 * e] = 0.0f;
-              if (!bf16_positive(w[e] >> 16)) v[8 * j + 2 * e + 1] = 0.0f;
+              if (p.act) {
+                v[8 * j + 2 * e] *= swish_grad(__uint_as_float(w[e] << 16));
+                v[8 * j + 2 * e + 1] *= swish_grad(__uint_as_float(w[e] & 0xFFFF0000u));
+              } else {
+                if (!bf16_positive(w[e] & 0xFFFFu)) v[8 * j + 2 * e] = 0.0f;
+                if (!bf16_positive(w[e] >> 16)) v[8 * j + 2 * e + 1] = 0.0f;
+              }
             }
           }
         }

@@ -38,6 +38,13 @@ struct TcGemmArgs {
   long long ldo;
   const float *w_out, *b_out;
   float *z_out;
+  // activation of the hidden layers: 0 ReLU, 1 Swish z sigmoid(z). With
+  // Swish, kTcFwd also stores the pre-activations z (BF16) in zpre, and
+  // kTcDx reads pre-activations from hprev and multiplies by the Swish
+  // derivative sigmoid(z) (1 + z (1 - sigmoid(z))) instead of the ReLU mask.
+  int act;
+  __nv_bfloat16 *zpre;
+  long long ldz;
   // kTcDx
   const __nv_bfloat16 *hprev;
   long long ldh;

@@ -41,6 +41,7 @@ struct TcState {
   std::vector<__nv_bfloat16 *> Wb, WbT;  // per hidden layer: [fan_out][kpad], [fan_in][W]
   std::vector<int> kpad;
   __nv_bfloat16 *E = nullptr, *H = nullptr, *D0 = nullptr, *D1 = nullptr;
+  __nv_bfloat16 *Z = nullptr;     // Swish: pre-activations, one buffer per activation buffer
   __nv_bfloat16 *Dall = nullptr;  // [H][samples][W] deltas of every layer (chain path)
   uint32_t *masks = nullptr;      // [H][samples][W/32] ReLU bits (chain path)
   float *rec = nullptr;           // per-ray records [samples][8] (chain path)
@@ -77,15 +78,24 @@ __global__ void k_to_bf16(const float *W, int rows, int cols, int kpad, __nv_bfl
   if (WbT && k < cols) WbT[(long long)k * rows + r] = b;
 }
 
-// delta_H[s][c] = dz[s] * w_out[c] * [h_H[s][c] > 0]
+// delta_H[s][c] = dz[s] * w_out[c] * act'(.): with ReLU [h_H[s][c] > 0] from
+// the activations, with Swish sigmoid(z)(1 + z(1 - sigmoid(z))) from the
+// pre-activations z passed in h.
 __global__ void k_out_delta_bf16(const float *dz, const float *w_out, const __nv_bfloat16 *h,
-                                 int W, long long n, __nv_bfloat16 *D) {
+                                 int W, long long n, int swish, __nv_bfloat16 *D) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= n * W) return;
   long long s = q / W;
   int col = (int)(q - s * W);
   float x = __bfloat162float(h[q]);
-  D[q] = __float2bfloat16_rn(x > 0.0f ? dz[s] * w_out[col] : 0.0f);
+  float g;
+  if (swish) {
+    const float sg = 1.0f / (1.0f + expf(-x));
+    g = sg * (1.0f + x * (1.0f - sg));
+  } else {
+    g = x > 0.0f ? 1.0f : 0.0f;
+  }
+  D[q] = __float2bfloat16_rn(dz[s] * w_out[col] * g);
 }
 
 // ---------------------------------------------------------------- FP8 (E4M3)
@@ -284,6 +294,10 @@ dinr_status gemm8(dinr_ctx *c, const char *name, double flops, double bytes, TcG
 __nv_bfloat16 *hid(dinr_ctx *c, int L, long long ns) {
   return S_(c)->H + (long long)h_slot(c, L) * ns * c->W;
 }
+// Swish pre-activations of layer L (same buffer slots as hid).
+__nv_bfloat16 *zid(dinr_ctx *c, int L, long long ns) {
+  return S_(c)->Z + (long long)h_slot(c, L) * ns * c->W;
+}
 
 // Forward GEMMs of layers [L0, L1) over ns samples whose features are in E
 // (the last layer also forms z_out).
@@ -309,6 +323,11 @@ dinr_status forward_layers(dinr_ctx *c, long long ns, int L0, int L1) {
     a.bias = c->d_params + c->offb[L];
     a.out = hid(c, L, ns);
     a.ldo = c->W;
+    if (c->act == DINR_ACT_SWISH) {
+      a.act = 1;
+      a.zpre = zid(c, L, ns);
+      a.ldz = c->W;
+    }
     if (last) {
       a.w_out = c->d_params + c->offW[c->H];
       a.b_out = c->d_params + c->offb[c->H];
@@ -361,10 +380,18 @@ dinr_status ensure_hidden(dinr_ctx *c, long long ns, int L) {
 
 int chain_k0(const dinr_ctx *c) { return (c->d_in + 63) / 64 * 64; }
 
+// GRFF matrix of the context into the chain's parameters (C = 128 only).
+void set_grff(const dinr_ctx *c, ChainArgs &a) {
+  a.grff_c = c->grff_c;
+  if (c->grff_c == kGrffChain) memcpy(a.grff_B, c->grff_B.data(), sizeof(a.grff_B));
+}
+
 bool chain_ok(const dinr_ctx *c) {
   if (c->prec != DINR_PREC_BF16) return false;  // the chains compute in BF16
-  if (!(c->W % 64 == 0 && c->W <= 256 && c->H <= kChainMaxLayers && chain_k0(c) <= 256 &&
-        chain_supports_freq(c->F) && chain_stages(c->W, chain_k0(c)) >= 2))
+  if (c->act != DINR_ACT_RELU) return false;    // the chains keep ReLU bits only
+  const bool enc = c->grff_c > 0 ? chain_supports_grff(c->grff_c) : chain_supports_freq(c->F);
+  if (!(c->W % 64 == 0 && c->W <= 256 && c->H <= kChainMaxLayers && chain_k0(c) <= 256 && enc &&
+        chain_stages(c->W, chain_k0(c)) >= 2))
     return false;
   // biases and output weights are read as float4
   for (int L = 0; L <= c->H; ++L)
@@ -394,6 +421,7 @@ dinr_status chain(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S, b
   a.n_rays = n_rays;
   a.S = S;
   a.F = c->F;
+  set_grff(c, a);
   a.d_in = c->d_in;
   a.k0 = chain_k0(c);
   a.W = c->W;
@@ -474,9 +502,11 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
   const int W = c->W;
   __nv_bfloat16 *hH = hid(c, c->H - 1, ns);
   // output layer: delta_H, grad w_out = sum dz h_H, grad b_out = sum dz
+  const bool swish = c->act == DINR_ACT_SWISH;
   if (!t->chain) {
     k_out_delta_bf16<<<ceil_div(ns * W, 256), 256, 0, c->st>>>(
-        t->dz, c->d_params + c->offW[c->H], hH, W, ns, t->D0);
+        t->dz, c->d_params + c->offW[c->H], swish ? zid(c, c->H - 1, ns) : hH, W, ns, swish,
+        t->D0);
     CKL();
   }
   int cs = colsum_splits(ns);
@@ -545,7 +575,8 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
       b.n_store = W;
       b.out = Dn;
       b.ldo = W;
-      b.hprev = hid(c, L - 1, ns);
+      b.act = swish ? 1 : 0;
+      b.hprev = swish ? zid(c, L - 1, ns) : hid(c, L - 1, ns);
       b.ldh = W;
       s = gemm(c, "tc_dx", 2.0 * ns * W * W, 2.0 * ns * 3 * W, b, D, ns, W, t->WbT[L], W, W);
       if (s != DINR_OK) return s;
@@ -578,9 +609,15 @@ bool tc_supported(const dinr_net *net) {
   // whole 32-column TMEM loads) or 512, 768, 1024 (256-wide N tiles); at
   // most 16 octaves (<= 144 padded inputs, one N tile of the first layer's
   // weight gradient).
+  // Swish runs on the unfused GEMMs; the first layer's input width (d_in
+  // padded to 16) must be one N tile (<= 256) of its weight gradient or whole
+  // 256-wide tiles.
   const int W = net->width;
-  return net->act == DINR_ACT_RELU && W % 32 == 0 && W >= 32 &&
-         (W <= 256 || (W % 256 == 0 && W <= 1024)) && net->n_freq <= 16;
+  const int d_in = net->encoding == DINR_ENC_GRFF ? 2 * net->grff_c : 4 + 8 * net->n_freq;
+  const int ld = (d_in + 15) / 16 * 16;
+  return (net->act == DINR_ACT_RELU || net->act == DINR_ACT_SWISH) && W % 32 == 0 && W >= 32 &&
+         (W <= 256 || (W % 256 == 0 && W <= 1024)) && net->n_freq <= 16 &&
+         (ld <= 256 || ld % 256 == 0);
 }
 
 static bool chains_used(const dinr_ctx *c) { return chain_ok(c) && c->H >= 2; }
@@ -592,7 +629,8 @@ bool tc_recompute_applies(const dinr_ctx *c) {
 long long tc_bytes_per_sample(const dinr_ctx *c) {
   if (chains_used(c))
     return 2LL * (c->ldE + 2LL * c->H * c->W) + (long long)c->H * c->W / 8 + 32 + 8 + 16;
-  return 2LL * (c->ldE + (long long)(n_hbuf(c) + 2) * c->W) + 8 + 16 +
+  return 2LL * (c->ldE + (long long)(n_hbuf(c) * (c->act == DINR_ACT_SWISH ? 2 : 1) + 2) * c->W) +
+         8 + 16 +
          (tiles_n(c->W) > 1 ? 4LL * tiles_n(c->W) : 0) +
          (c->prec == DINR_PREC_FP8 ? c->ldE + 2LL * c->W : 0);
 }
@@ -655,6 +693,7 @@ dinr_status tc_alloc(dinr_ctx *c) {
     }
   }
   if (tiles_n(c->W) > 1) ok = ok && grab((void **)&t->zpart, 4ull * ns * tiles_n(c->W));
+  if (c->act == DINR_ACT_SWISH) ok = ok && grab((void **)&t->Z, 2ull * ns * c->W * n_hbuf(c));
   ok = ok && grab((void **)&t->E, 2ull * ns * c->ldE) &&
        grab((void **)&t->H, 2ull * ns * c->W * n_hbuf(c)) && grab((void **)&t->zout, 4ull * ns) &&
        grab((void **)&t->dz, 4ull * ns) && grab((void **)&t->ray_l, 4ull * ns) &&
@@ -707,7 +746,7 @@ dinr_status tc_loss_grad(dinr_ctx *c, int n) {
     } else {
       {
         ProfScope ps(c, "encode", 0.0, 2.0 * ns * c->ldE);
-        launch_encode_bf16(c->geo, src, nr, c->S, c->F, c->ldE, t->E, t->ray_l, c->d_proj,
+        launch_encode_bf16(c->geo, src, nr, c->S, c->F, c->grff_c, c->d_grff_B, c->ldE, t->E, t->ray_l, c->d_proj,
                            t->ray_p, c->st);
         CKL();
       }
@@ -746,7 +785,7 @@ static dinr_status tc_forward(dinr_ctx *c, const SourceArgs &src0, long long n_r
     if (chain_ok(c)) {
       s = chain(c, src, nr, S, false, nullptr);
     } else {
-      launch_encode_bf16(c->geo, src, nr, S, c->F, c->ldE, t->E, t->ray_l, nullptr, nullptr,
+      launch_encode_bf16(c->geo, src, nr, S, c->F, c->grff_c, c->d_grff_B, c->ldE, t->E, t->ray_l, nullptr, nullptr,
                          c->st);
       CKL();
       s = forward(c, ns);
@@ -817,6 +856,7 @@ dinr_status tc_serve_chain(dinr_ctx *c, const WorkItem *items, const int *tile_i
   ChainArgs a{};
   a.g = c->geo;
   a.F = c->F;
+  set_grff(c, a);
   a.d_in = c->d_in;
   a.k0 = chain_k0(c);
   a.W = c->W;

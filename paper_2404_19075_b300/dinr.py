@@ -42,7 +42,13 @@ def _cuda_i64(x):
 
 
 def param_count(n_freq, hidden_layers, width) -> int:
+    """Parameters of an octave-encoded network."""
     return int(_abi.lib().dinr_param_count(n_freq, hidden_layers, width))
+
+
+def param_count_net(net) -> int:
+    """Parameters of a network description (any encoding)."""
+    return int(_abi.lib().dinr_param_count_din(net.d_in, net.hidden_layers, net.width))
 
 
 def geometry_struct(g):
@@ -71,16 +77,22 @@ class Dinr:
         L = _abi.lib()
         self.geometry, self.net = geometry, net
         gs, self._keep = geometry_struct(geometry)
-        self.n_params = param_count(net.n_freq, net.hidden_layers, net.width)
+        self.n_params = param_count_net(net)
         init = None
         if init_params is not None:
             init = np.ascontiguousarray(init_params, np.float32)
             if init.size != self.n_params:
                 raise ValueError("init_params has the wrong length")
+        enc = getattr(net, "encoding", "octave")
+        B = None
+        if enc == "grff":
+            B = np.ascontiguousarray(net.grff_B, np.float32)
+            self._keep = self._keep + (B,)
         ns = _abi.Net(net.n_freq, net.hidden_layers, net.width,
                       _abi.ACT[net.act], _abi.OUT_ACT[net.out_act], _abi.PREC[prec],
                       init.ctypes.data_as(C.POINTER(C.c_float)) if init is not None else None,
-                      seed)
+                      seed, _abi.ENCODING[enc], net.grff_c if B is not None else 0,
+                      B.ctypes.data_as(C.POINTER(C.c_float)) if B is not None else None)
         ts = _abi.Train(train.lr, train.beta1, train.beta2, train.eps,
                         getattr(train, "lr_decay_per_epoch", 1.0), train.batch_rays,
                         chunk_rays, sampler_seed, recompute)

@@ -67,10 +67,24 @@ class Net:
     width: int
     act: str = "relu"             # "relu" or "swish"
     out_act: str = "identity"     # "identity" or "softplus"
+    encoding: str = "octave"      # "octave" or "grff" (Gaussian random Fourier features)
+    grff_c: int = 0               # C frequencies (2C features) of the GRFF encoding
+    sigma_t: float = 0.1          # std of B's time column
+    sigma_s: float = 0.5          # std of B's three spatial columns
+    grff_seed: int = 0
 
     @property
     def d_in(self) -> int:
-        return 4 + 8 * self.n_freq
+        return 2 * self.grff_c if self.encoding == "grff" else 4 + 8 * self.n_freq
+
+    @property
+    def grff_B(self) -> np.ndarray:
+        """The frozen GRFF matrix B [C][4] (columns t, z, y, x): normals of
+        the stream grff_seed, column 0 scaled by sigma_t and columns 1-3 by
+        sigma_s, rounded to FP32 once so both sides use the same values."""
+        z = rng.normal(self.grff_seed, 4 * self.grff_c).reshape(self.grff_c, 4)
+        sig = np.array([self.sigma_t, self.sigma_s, self.sigma_s, self.sigma_s])
+        return (z * sig).astype(np.float32).astype(np.float64)
 
     def layer_shapes(self):
         """(fan_out, fan_in) of each linear layer, output layer last."""
@@ -147,8 +161,11 @@ def _views(n, rotations):
 
 
 def workload(c: int) -> Workload:
-    """The five workloads: 1 parity, 2 parallel-beam perf, 3 cone-beam,
-    4 wide network at scale, 5 serving (network of 3)."""
+    """The workloads: 1 parity, 2 parallel-beam perf, 3 cone-beam, 4 wide
+    network at scale, 5 serving (network of 3), 6 the paper's own network
+    (GRFF encoding 2C = 256 with sigma_s = 0.5, sigma_t = 0.1, five Swish
+    layers of 2C, linear output) on the geometry of 2, 7 the same network
+    at parity size (geometry of 1, 2C = 64, three layers)."""
     if c == 1:
         k = np.arange(64, dtype=np.float64)
         g = parallel_geometry(64, 32, 32, math.pi * k / 64, k / 64, 32)
@@ -172,6 +189,17 @@ def workload(c: int) -> Workload:
     if c == 5:
         w = workload(3)
         return replace(w, index=5, name="serving: trained 6x256 cone-beam network")
+    if c == 6:
+        w = workload(2)
+        net = Net(0, 5, 256, "swish", "identity", "grff", 128, 0.1, 0.5, 6006)
+        return replace(w, index=6, net=net,
+                       name="parallel-beam 512 views 128x128, S=128, GRFF 2C=256 + 5x256 Swish, "
+                            "B=65536")
+    if c == 7:
+        w = workload(1)
+        net = Net(0, 3, 64, "swish", "identity", "grff", 32, 0.1, 0.5, 6007)
+        return replace(w, index=7, net=net,
+                       name="parallel-beam 64 views 32x32, S=32, GRFF 2C=64 + 3x64 Swish, B=1024")
     raise ValueError(f"no workload {c}")
 
 

@@ -43,6 +43,9 @@ def test_param_count_host_function(abi):
         net = wl.workload(c).net
         assert L.dinr_param_count(net.n_freq, net.hidden_layers, net.width) == net.n_params
     assert L.dinr_param_count(-1, 3, 64) == -1
+    for c in (6, 7):
+        net = wl.workload(c).net
+        assert L.dinr_param_count_din(net.d_in, net.hidden_layers, net.width) == net.n_params
 
 
 def test_product_never_imports_the_oracle():

@@ -228,3 +228,54 @@ def test_bf16_decisions_only_change_near_kinks():
     M1, _ = network.forward(theta, net, e, exact)
     M0, _ = network.forward(theta, net, e)
     assert np.array_equal(M1, M0)
+
+
+# ---------------------------------------------------------- GRFF (App. B)
+
+def test_grff_reproduces_octave_features():
+    """cos/sin(2 pi b . r) with b = 2^(l-1) e_k is the octave feature
+    sin/cos(2^l pi r_k): pins the 2 pi, B's orientation (row per frequency,
+    column per coordinate t, z, y, x) and the cosines-first order."""
+    F = 5
+    rbar = np.random.default_rng(0).uniform(-1, 1, (50, 4))
+    rows = [(k, l) for k in range(4) for l in range(F)]
+    B = np.zeros((len(rows), 4))
+    for i, (k, l) in enumerate(rows):
+        B[i, k] = 2.0 ** (l - 1)
+    g = network.encode_grff(rbar, B)
+    o = network.encode(rbar, F)
+    C = len(rows)
+    for i, (k, l) in enumerate(rows):
+        col = 4 + 2 * F * k + 2 * l          # octave layout: sin, cos
+        assert np.allclose(g[:, C + i], o[:, col], atol=1e-12)
+        assert np.allclose(g[:, i], o[:, col + 1], atol=1e-12)
+
+
+def test_grff_zero_matrix_and_unit_pairs():
+    rbar = np.random.default_rng(1).uniform(-1, 1, (20, 4))
+    g0 = network.encode_grff(rbar, np.zeros((8, 4)))
+    assert np.array_equal(g0[:, :8], np.ones((20, 8))) and np.array_equal(g0[:, 8:], np.zeros((20, 8)))
+    B = wl.workload(6).net.grff_B
+    g = network.encode_grff(rbar, B)
+    C = B.shape[0]
+    assert np.allclose(g[:, :C] ** 2 + g[:, C:] ** 2, 1.0, atol=1e-12)
+
+
+def test_grff_matrix_columns():
+    """Column 0 (time) has std sigma_t, columns 1-3 (z, y, x) sigma_s; values
+    are FP32-representable so the GPU gets exactly the oracle's B."""
+    from dataclasses import replace
+    net = replace(wl.workload(6).net, grff_c=20000)
+    B = net.grff_B
+    sd = B.std(axis=0)
+    assert abs(sd[0] / net.sigma_t - 1) < 0.03
+    assert np.all(np.abs(sd[1:] / net.sigma_s - 1) < 0.03)
+    assert np.array_equal(B, B.astype(np.float32).astype(np.float64))
+
+
+def test_paper_network_parameter_count():
+    """2C = 256 GRFF inputs, L = 5 Swish layers of 256, linear output: the
+    parameter count the paper prints (329,217)."""
+    net = wl.workload(6).net
+    assert (net.d_in, net.hidden_layers, net.width, net.act) == (256, 5, 256, "swish")
+    assert net.n_params == 329217
