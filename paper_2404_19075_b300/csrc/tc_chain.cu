@@ -108,6 +108,34 @@ __device__ __forceinline__ uint2 ld_stream2(const uint32_t *p) {
                : "l"(p));
   return v;
 }
+__device__ __forceinline__ uint4 ld_stream16(const void *p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_stream16(void *p, uint4 v) {
+  asm volatile("st.global.L1::no_allocate.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x),
+               "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+// Low / high BF16 half of a packed pair, as FP32.
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// Swish z sigmoid(z) and its derivative sigmoid(z)(1 + z(1 - sigmoid(z))),
+// with sigmoid(z) = 1 / (1 + 2^(-z log2 e)) from the hardware exp2 and
+// reciprocal (relative error about 2^-22 for every z; a tanh-based sigmoid
+// loses relative accuracy for negative z, where 1/2 + tanh/2 cancels).
+__device__ __forceinline__ void swish_fg(float z, float &h, float &g) {
+  float e, sg;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-1.4426950408889634f * z));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sg) : "f"(1.0f + e));
+  h = z * sg;
+  g = sg * fmaf(z, 1.0f - sg, 1.0f);
+}
+
 __device__ __forceinline__ void st_stream2(uint32_t *p, uint2 v) {
   asm volatile("st.global.L1::no_allocate.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(v.x), "r"(v.y)
                : "memory");
@@ -379,8 +407,60 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
   }
 }
 
-// After layer L of one tile: bias + ReLU, BF16 back into the tile buffer,
-// TMA store of h_L, and on the last layer the output dot product.
+// Swish part of the forward epilogue for one 64-column chunk: h = swish(z)
+// into the tile buffer (32 columns at a time), the derivative g into
+// gact[L] (the backward's factor in place of the ReLU mask), and on the last
+// layer the output dot product.
+__device__ __forceinline__ void swish_chunk(const ChainArgs &p, uint8_t *chunk, int jc, int L,
+                                            uint32_t trow, int r_in, long long row, bool live,
+                                            bool last, float &dot) {
+  const float *bias = p.bias[L];
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    const int c0 = 64 * jc + 32 * hh;
+    float4 bb[8];
+#pragma unroll
+    for (int i4 = 0; i4 < 8; ++i4) bb[i4] = ld_keep(bias + c0 + 4 * i4);
+    float v[32];
+    tmem_ld32(trow + c0, v);
+    uint32_t wh[16], wg[16];
+#pragma unroll
+    for (int i4 = 0; i4 < 8; ++i4) {
+      const float4 b = bb[i4];
+      const float z[4] = {v[4 * i4] + b.x, v[4 * i4 + 1] + b.y, v[4 * i4 + 2] + b.z,
+                          v[4 * i4 + 3] + b.w};
+      float h[4], g[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) swish_fg(z[e], h[e], g[e]);
+      wh[2 * i4] = pack2(h[0], h[1]);
+      wh[2 * i4 + 1] = pack2(h[2], h[3]);
+      wg[2 * i4] = pack2(g[0], g[1]);
+      wg[2 * i4 + 1] = pack2(g[2], g[3]);
+      if (last) {
+        const float4 o = ld_keep(p.w_out + c0 + 4 * i4);
+        dot = fmaf(h[0], o.x, dot);
+        dot = fmaf(h[1], o.y, dot);
+        dot = fmaf(h[2], o.z, dot);
+        dot = fmaf(h[3], o.w, dot);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      *reinterpret_cast<uint4 *>(chunk + swz(r_in, 4 * hh + u)) =
+          make_uint4(wh[4 * u], wh[4 * u + 1], wh[4 * u + 2], wh[4 * u + 3]);
+    if (live && p.gact[L]) {
+      uint8_t *gp = reinterpret_cast<uint8_t *>(p.gact[L] + row * p.W + c0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        st_stream16(gp + 16 * u, make_uint4(wg[4 * u], wg[4 * u + 1], wg[4 * u + 2], wg[4 * u + 3]));
+    }
+  }
+}
+
+// After layer L of one tile: bias + activation, BF16 back into the tile
+// buffer, ReLU bits (or the Swish derivative), TMA store of h_L, and on the
+// last layer the output dot product.
+template <int kAct>
 __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
                                int slot, uint32_t tcol, int L, long long tile, int q, int half,
                                int lane, uint32_t dot_phase) {
@@ -393,6 +473,10 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
   uint8_t *A = s.A[slot];
   float dot = 0.0f;
   for (int jc = half; jc < p.W / 64; jc += 2) {
+    if constexpr (kAct == kActSwish) {
+      swish_chunk(p, A + (size_t)jc * kChunkBytes, jc, L, trow, r_in, row, live, last, dot);
+      continue;
+    }
     // bias of the chunk first, so that its load overlaps the TMEM load
     float4 bb[16];
 #pragma unroll
@@ -466,13 +550,36 @@ __device__ __forceinline__ void store_chunks(const ChainMaps &maps, const ChainA
   }
 }
 
-// delta_{H-1}[s][c] = dz[s] * w_out[c] * [h_{H-1}[s][c] > 0] into the tile buffer.
+// delta_{H-1}[s][c] = dz[s] * w_out[c] * act'(.) into the tile buffer: the
+// ReLU bit of h_{H-1}, or the stored Swish derivative.
+template <int kAct>
 __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t *A,
                              long long tile, int q, int half, int lane) {
   const int r_in = q * 32 + lane;
   const long long row = tile * 128 + r_in;
   const bool live = row < p.ns;
   const float dzr = live ? p.dz[row] : 0.0f;
+  if constexpr (kAct == kActSwish) {
+    const uint8_t *grow = reinterpret_cast<const uint8_t *>(p.gact[p.H - 1] + (live ? row : 0) * p.W);
+    for (int jc = half; jc < p.W / 64; jc += 2) {
+      uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+#pragma unroll
+      for (int c16 = 0; c16 < 8; ++c16) {
+        const uint4 gq = live ? ld_stream16(grow + 128 * jc + 16 * c16) : make_uint4(0, 0, 0, 0);
+        const uint32_t gw[4] = {gq.x, gq.y, gq.z, gq.w};
+        const float4 oa = ld_keep(p.w_out + 64 * jc + 8 * c16);
+        const float4 ob = ld_keep(p.w_out + 64 * jc + 8 * c16 + 4);
+        const float o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          w[e] = pack2(dzr * o[2 * e] * bf_lo(gw[e]), dzr * o[2 * e + 1] * bf_hi(gw[e]));
+        *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    store_chunks(maps, p, A, p.H - 1, tile, q, half, lane);
+    return;
+  }
   const uint32_t *mrow = p.masks[p.H - 1] + (live ? row : 0) * (p.W / 32);
   for (int jc = half; jc < p.W / 64; jc += 2) {
     const uint2 mb = live ? ld_stream2(mrow + 2 * jc) : make_uint2(0u, 0u);
@@ -493,10 +600,58 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
   store_chunks(maps, p, A, p.H - 1, tile, q, half, lane);
 }
 
+// Swish: delta_{L-1} = acc * g_{L-1} with the derivative the forward stored;
+// the first chunk's factors are loaded before the wait.
+__device__ bool bwd_epilogue_swish(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
+                                   int slot, uint32_t tcol, int L, long long tile, int q, int half,
+                                   int lane, uint32_t tfull_phase) {
+  const int r_in = q * 32 + lane;
+  const long long row = tile * 128 + r_in;
+  const bool live = row < p.ns;
+  const uint8_t *grow = reinterpret_cast<const uint8_t *>(p.gact[L - 1] + (live ? row : 0) * p.W);
+  uint4 gq[8];
+#pragma unroll
+  for (int c16 = 0; c16 < 8; ++c16)
+    gq[c16] = live && half < p.W / 64 ? ld_stream16(grow + 128 * half + 16 * c16)
+                                      : make_uint4(0, 0, 0, 0);
+  if (!warp_wait(&s.tfull[slot], tfull_phase & 1, p.err, 18)) return false;
+  tc_fence_after();
+  if (lane == 0) bulk_wait_read();
+  __syncwarp();
+  const uint32_t trow = tcol + ((uint32_t)(q * 32) << 16);
+  uint8_t *A = s.A[slot];
+  for (int jc = half; jc < p.W / 64; jc += 2) {
+    if (jc != half) {
+#pragma unroll
+      for (int c16 = 0; c16 < 8; ++c16)
+        gq[c16] = live ? ld_stream16(grow + 128 * jc + 16 * c16) : make_uint4(0, 0, 0, 0);
+    }
+    float v[64];
+    tmem_ld64(trow + 64 * jc, v);
+    uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+#pragma unroll
+    for (int c16 = 0; c16 < 8; ++c16) {
+      const uint32_t gw[4] = {gq[c16].x, gq[c16].y, gq[c16].z, gq[c16].w};
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = 8 * c16 + 2 * e;
+        w[e] = pack2(v[i] * bf_lo(gw[e]), v[i + 1] * bf_hi(gw[e]));
+      }
+      *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  store_chunks(maps, p, A, L - 1, tile, q, half, lane);
+  return true;
+}
+
 // After the input-gradient GEMM through layer L: delta_{L-1} = acc * [h_{L-1} > 0].
+template <int kAct>
 __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Smem &s, int slot,
                              uint32_t tcol, int L, long long tile, int q, int half, int lane,
                              uint32_t tfull_phase) {
+  if constexpr (kAct == kActSwish)
+    return bwd_epilogue_swish(maps, p, s, slot, tcol, L, tile, q, half, lane, tfull_phase);
   const int r_in = q * 32 + lane;
   const long long row = tile * 128 + r_in;
   const bool live = row < p.ns;
@@ -534,7 +689,7 @@ __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Sm
 
 // ------------------------------------------------------- epilogue warps
 
-template <int F, bool kBwd>
+template <int F, bool kBwd, int kAct>
 __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
                                uint32_t tbase) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -548,7 +703,7 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
   };
   auto start_tile = [&](int slot, long long tile) {
     if (kBwd)
-      bwd_prologue(maps, p, s.A[slot], tile, q, half, lane);
+      bwd_prologue<kAct>(maps, p, s.A[slot], tile, q, half, lane);
     else
       encode_tile<F>(maps, p, s.A[slot], tile, q, half, lane);
   };
@@ -564,14 +719,14 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
         const bool last = i == ns - 1;
         const uint32_t tcol = tbase + (uint32_t)(slot * p.W);
         if (kBwd) {
-          if (!bwd_epilogue(maps, p, s, slot, tcol, step_layer<true>(p, i), tile, q, half, lane,
+          if (!bwd_epilogue<kAct>(maps, p, s, slot, tcol, step_layer<true>(p, i), tile, q, half, lane,
                             waits[slot]++))
             return;
         } else {
           if (!warp_wait(&s.tfull[slot], waits[slot]++ & 1, p.err, 17)) return;
           tc_fence_after();
           wait_stores();
-          if (!epilogue_layer(maps, p, s, slot, tcol, i, tile, q, half, lane,
+          if (!epilogue_layer<kAct>(maps, p, s, slot, tcol, i, tile, q, half, lane,
                               last ? dots[slot]++ : 0))
             return;
         }
@@ -586,7 +741,7 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
       }
 }
 
-template <int F, bool kBwd>
+template <int F, bool kBwd, int kAct>
 __global__ void __launch_bounds__(kThreads, 1)
     k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainArgs p) {
   extern __shared__ uint8_t smem_raw[];
@@ -619,7 +774,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) mma_issuer<kBwd>(p, s, tbase);
   } else {
-    epilogue_warps<F, kBwd>(maps, p, s, tbase);
+    epilogue_warps<F, kBwd, kAct>(maps, p, s, tbase);
     if (lane == 0) bulk_wait_all();
   }
   tc_fence_before();
@@ -646,15 +801,21 @@ int chain_stages(int W, int k0) {
 bool chain_supports_freq(int F) { return F == 6 || F == 8 || F == 10 || F == 12 || F == 16; }
 bool chain_supports_grff(int C) { return C == kGrffChain; }
 
-template <int F, bool kBwd>
-static int launch_f(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
+template <int F, bool kBwd, int kAct>
+static int launch_fa(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
   size_t smem = chain_smem_bytes(a.W, a.k0, a.stages);
-  cudaError_t e = cudaFuncSetAttribute(k_chain<F, kBwd>,
+  cudaError_t e = cudaFuncSetAttribute(k_chain<F, kBwd, kAct>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   int grid = a.m_tiles < num_sms ? a.m_tiles : num_sms;
-  k_chain<F, kBwd><<<grid, kThreads, smem, st>>>(maps, a);
+  k_chain<F, kBwd, kAct><<<grid, kThreads, smem, st>>>(maps, a);
   return (int)cudaGetLastError();
+}
+
+template <int F, bool kBwd>
+static int launch_f(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {
+  return a.act == kActSwish ? launch_fa<F, kBwd, kActSwish>(maps, a, num_sms, st)
+                            : launch_fa<F, kBwd, kActRelu>(maps, a, num_sms, st);
 }
 
 int launch_fwd_chain(const ChainMaps &maps, const ChainArgs &a, int num_sms, cudaStream_t st) {

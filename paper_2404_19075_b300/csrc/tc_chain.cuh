@@ -13,6 +13,8 @@ constexpr int kChainMaxLayers = 8;
 // Template value of the encoding for Gaussian random Fourier features with
 // C = 128 (2C = 256 inputs); octave encodings use F itself (<= 16).
 constexpr int kGrffChain = 128;
+// Hidden-layer activation of a chain.
+constexpr int kActRelu = 0, kActSwish = 1;
 
 // One piece of a serving batch: samples [0, n) of a query, starting at tile
 // tile0 of the batch (items start on 128-sample tile boundaries).
@@ -52,7 +54,9 @@ struct ChainArgs {
   float *ray_l, *ray_p;            // [n_rays]
   const float *rays;               // per-ray records [n_rays][8] (ray sources), see
                                    // launch_ray_records
-  uint32_t *masks[kChainMaxLayers];  // ReLU bits of h_L: [samples][W/32] words
+  int act;                         // kActRelu or kActSwish
+  uint32_t *masks[kChainMaxLayers];  // ReLU: bits of h_L, [samples][W/32] words
+  __nv_bfloat16 *gact[kChainMaxLayers];  // Swish: derivative at z_L, [samples][W] BF16
   const float *proj;               // measured stack (training rays) or null
   // serving batches: per-tile work items (null for a single source)
   const WorkItem *items;

