@@ -366,6 +366,16 @@ def run_serving(args, rank):
         res = serving.run(m, qs, time_limit=120.0)
     m.profile(False)
     prof = m.profile_report()
+    # 4D export: 8 volumes of 256^3 streamed to pinned host memory
+    ex_dims, ex_times = (256, 256, 256), [(k + 0.5) / 8 for k in range(8)]
+    sums = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.export(ex_times, (-1, -1, -1), (1, 1, 1), ex_dims, lambda k, t, vol: sums.append(float(vol[0, 0, 0])))
+    ex_wall = time.perf_counter() - t0
+    n_vox = len(ex_times) * ex_dims[0] * ex_dims[1] * ex_dims[2]
+    export = {"volumes": len(ex_times), "dims": list(ex_dims), "wall_s": ex_wall,
+              "voxels_per_s": n_vox / ex_wall, "host_gb_per_s": 4 * n_vox / ex_wall / 1e9}
     m.close()
     chain = prof.get("tc_serve_chain", {"ms": float("nan"), "flops": 0, "launches": 0})
     pk, src = peaks()
@@ -383,6 +393,7 @@ def run_serving(args, rank):
                       "frac_of_bf16_sustained": tf / pk["bf16_tflops_sustained"] if tf else None,
                       "peak_source": f"bf16_tflops_sustained ({src})"},
             "gpu_launches": prof.get("total_launches", {}).get("launches"),
+            "export_4d": export,
             "clocks": ck.summary(),
             "config": "cone beam SOD 4 / SDD 8, MLP 6x256 ReLU, 10-octave encoding; "
                       "slices 128^2..1024^2, sub-volumes 32^3..256^3, re-projections "

@@ -221,6 +221,19 @@ DINR_API dinr_status dinr_query(dinr_ctx *ctx, const float *coords_dev, int64_t 
 DINR_API dinr_status dinr_query_grid(dinr_ctx *ctx, double t, const double *lo,
                             const double *hi, const int *dims, float *out_dev);
 
+/* 4D export (Sec. V: the reconstruction at every view time). For each
+ * times[k] the grid of dinr_query_grid (lo, hi, dims as there) is computed
+ * and copied to pinned host memory while the next volume is computed; then
+ * sink(user, k, times[k], volume, n) is called on the calling thread, in
+ * order k = 0, 1, ..., with volume valid until the sink returns (host
+ * float[nz*ny*nx], x fastest). A nonzero return from the sink stops the
+ * export (DINR_ERR_STATE). Uses two device and two pinned host volumes of
+ * 4 * nx * ny * nz bytes for the duration of the call. Synchronous. */
+typedef int (*dinr_volume_sink)(void *user, int k, double t, const float *volume, int64_t n);
+DINR_API dinr_status dinr_export(dinr_ctx *ctx, const double *times, int n_times,
+                                 const double *lo, const double *hi, const int *dims,
+                                 dinr_volume_sink sink, void *user);
+
 /* ----------------------------------------------------------------------
  * Query server (Sec. V: inference from the trained network). Requests of
  * different kinds and sizes are batched continuously: each dinr_serve_step

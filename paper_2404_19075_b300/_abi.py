@@ -59,6 +59,10 @@ class Request(C.Structure):
 
 QUERY = {"points": 0, "grid": 1, "project": 2}
 
+# dinr_volume_sink(user, k, t, volume, n) -> int
+VOLUME_SINK = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_float),
+                          C.c_int64)
+
 vp, i64 = C.c_void_p, C.c_int64
 PROTOTYPES = {
     "dinr_param_count": (C.c_int64, [C.c_int, C.c_int, C.c_int]),
@@ -73,6 +77,8 @@ PROTOTYPES = {
     "dinr_query": (C.c_int, [vp, vp, i64, vp]),
     "dinr_query_grid": (C.c_int, [vp, C.c_double, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.POINTER(C.c_int), vp]),
+    "dinr_export": (C.c_int, [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
+                              C.POINTER(C.c_double), C.POINTER(C.c_int), VOLUME_SINK, vp]),
     "dinr_set_params": (C.c_int, [vp, vp, C.c_int]),
     "dinr_get_params": (C.c_int, [vp, vp, C.c_int]),
     "dinr_get_grads": (C.c_int, [vp, vp]),

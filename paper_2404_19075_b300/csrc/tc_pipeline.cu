@@ -181,7 +181,35 @@ __global__ void __launch_bounds__(256)
   float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, blk[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (rl < lanes) {
     int n = 0;
-    for (long long r = r0 + rl; r < r1; r += lanes) {
+    long long r = r0 + rl;
+    // four rows per step: their loads are in flight together
+    for (; r + 3 * (long long)lanes < r1; r += 4 * (long long)lanes) {
+      uint4 u[4];
+      float wr[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        u[k] = *reinterpret_cast<const uint4 *>(X + (r + k * lanes) * C + 8 * cv);
+        wr[k] = w[r + k * lanes];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t v[4] = {u[k].x, u[k].y, u[k].z, u[k].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          blk[2 * e] += wr[k] * __uint_as_float(v[e] << 16);
+          blk[2 * e + 1] += wr[k] * __uint_as_float(v[e] & 0xFFFF0000u);
+        }
+      }
+      if ((n += 4) == 256) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          acc[k] += blk[k];
+          blk[k] = 0.0f;
+        }
+        n = 0;
+      }
+    }
+    for (; r < r1; r += lanes) {
       const uint4 u = *reinterpret_cast<const uint4 *>(X + r * C + 8 * cv);
       const float wr = w[r];
       const uint32_t v[4] = {u.x, u.y, u.z, u.w};
@@ -189,14 +217,6 @@ __global__ void __launch_bounds__(256)
       for (int e = 0; e < 4; ++e) {
         blk[2 * e] += wr * __uint_as_float(v[e] << 16);
         blk[2 * e + 1] += wr * __uint_as_float(v[e] & 0xFFFF0000u);
-      }
-      if (++n == 256) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          acc[k] += blk[k];
-          blk[k] = 0.0f;
-        }
-        n = 0;
       }
     }
   }

@@ -194,6 +194,23 @@ class Dinr:
         self._c(_abi.lib().dinr_query_grid(self._h, float(t), lo_a, hi_a, d_a, _ptr(out)))
         return out.view(dims[2], dims[1], dims[0])
 
+    def export(self, times, lo, hi, dims, sink):
+        """4D export: sink(k, t, volume) for each time in order, volume a
+        host float32 array [nz, ny, nx] valid during the call (copy it to
+        keep it); a sink returning True stops the export (DinrError)."""
+        t = np.ascontiguousarray(times, np.float64)
+        lo_a, hi_a = (C.c_double * 3)(*lo), (C.c_double * 3)(*hi)
+        d_a = (C.c_int * 3)(*dims)
+        shape = (dims[2], dims[1], dims[0])
+
+        def _cb(user, k, tk, ptr, n):
+            vol = np.ctypeslib.as_array(ptr, shape=(n,)).reshape(shape)
+            return 1 if sink(k, tk, vol) else 0
+
+        cb = _abi.VOLUME_SINK(_cb)
+        self._c(_abi.lib().dinr_export(self._h, t.ctypes.data_as(C.POINTER(C.c_double)), t.size,
+                                       lo_a, hi_a, d_a, cb, None))
+
     # -- query server (continuous batching)
     def serve_config(self, max_batch_samples=0, max_inflight_bytes=0):
         self._c(_abi.lib().dinr_serve_config(self._h, int(max_batch_samples),

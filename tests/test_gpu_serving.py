@@ -150,3 +150,22 @@ def test_poisson_stream_completes(model):
             m.serve_step()
         torch.cuda.synchronize()
         assert torch.equal(out, res["outputs"][i])
+
+
+def test_export_4d(model):
+    """4D export: volumes arrive in order, each bitwise the grid query of its
+    time; a sink that asks to stop ends the export with an error."""
+    from paper_2404_19075_b300 import DinrError
+    w, m, theta = model
+    times = [0.1, 0.45, 0.8, 0.95]
+    lo, hi, dims = (-1, -1, -1), (1, 1, 1), (20, 16, 12)
+    got = []
+    m.export(times, lo, hi, dims, lambda k, t, vol: got.append((k, t, vol.copy())))
+    assert [g[0] for g in got] == [0, 1, 2, 3] and [g[1] for g in got] == times
+    for k, t, vol in got:
+        assert vol.shape == (12, 16, 20)
+        assert np.array_equal(vol, m.query_grid(t, lo, hi, dims).cpu().numpy())
+    seen = []
+    with pytest.raises(DinrError):
+        m.export(times, lo, hi, dims, lambda k, t, vol: seen.append(k) or k == 1)
+    assert seen == [0, 1]
