@@ -139,3 +139,51 @@ def voxel_pitch(det_pitch: float, sod: float, sdd: float) -> float:
     """Sec. V (Discussion): the reconstruction voxel is the detector pixel
     divided by the geometric magnification SDD/SOD."""
     return det_pitch / (sdd / sod)
+
+
+# ------------------------------------------------- App. A forward model
+
+def sample_spacing(geom) -> float:
+    """App. A: the spacing of samples along a ray is the pixel size
+    back-projected onto the object (through the rotation axis: times
+    SOD/SDD for a cone beam) divided by the sub-pixel factor D."""
+    pitch = min(geom.det_pitch_u, geom.det_pitch_v)
+    if geom.beam == "cone":
+        pitch *= geom.sod / geom.sdd
+    return pitch / geom.subpixels
+
+
+def subpixel_rays(geom, idx):
+    """App. A: D x D rays per pixel, to the centres of its D x D sub-pixels;
+    ray k of pixel p is sub-pixel (a, b) = (k div D, k mod D), a along the
+    detector rows (v), b along the columns (u). Returns o, d, s0, l, t per
+    ray, pixel-major ([n * D * D])."""
+    D = geom.subpixels
+    m, row, col = decode(idx, geom.n_pixels, geom.det_cols)
+    a = (np.arange(D)[:, None] * np.ones((1, D))).reshape(-1)     # row sub-index
+    b = (np.ones((D, 1)) * np.arange(D)[None, :]).reshape(-1)     # column sub-index
+    u = geom.det_off_u + (col[:, None] + (b[None, :] + 0.5) / D) * geom.det_pitch_u
+    v = geom.det_off_v + (row[:, None] + (a[None, :] + 0.5) / D) * geom.det_pitch_v
+    theta = np.repeat(np.asarray(geom.view_angle)[m][:, None], D * D, axis=1)
+    o, d = rays_at(geom, theta, u, v)
+    o, d = o.reshape(-1, 3), d.reshape(-1, 3)
+    s0, l = fov_chord(geom, o, d)
+    t = np.repeat(np.asarray(geom.view_time)[m], D * D)
+    return o, d, s0, l, t
+
+
+def subpixel_counts(geom, l):
+    """Samples per ray: the fewest equal sub-intervals of the chord no
+    longer than the spacing, ceil(l / spacing); 0 for an empty chord."""
+    n = np.ceil(np.asarray(l, np.float64) / sample_spacing(geom))
+    return np.where(np.asarray(l) > 0, np.maximum(n, 1), 0).astype(np.int64)
+
+
+def subpixel_samples(o, d, s0, l, n):
+    """Midpoints of n[k] equal sub-intervals of each chord, concatenated ray
+    by ray. Returns points [sum n, 3] and the ray of each sample."""
+    ray = np.repeat(np.arange(len(n)), n)
+    first = np.concatenate([[0], np.cumsum(n)[:-1]])
+    j = np.arange(ray.size) - first[ray]
+    s = s0[ray] + (j + 0.5) * l[ray] / n[ray]
+    return o[ray] + s[:, None] * d[ray], ray

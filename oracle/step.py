@@ -30,6 +30,27 @@ def encoded_samples(geom, net, idx):
     return e.reshape(-1, net.d_in), l
 
 
+def subpixel_model(geom, net, idx):
+    """App. A forward model of the minibatch: D x D rays per pixel, samples
+    about Delta/D apart inside the FOV. Returns the features of all samples
+    (ray by ray, pixel by pixel), each sample's weight factor mu0 * l of
+    its ray (Eq. 2), each sample's pixel and |Phi_i| of each pixel."""
+    D2 = geom.subpixels ** 2
+    o, d, s0, l, t = geometry.subpixel_rays(geom, idx)
+    n = geometry.subpixel_counts(geom, l)
+    P, ray = geometry.subpixel_samples(o, d, s0, l, n)
+    rbar = geometry.normalize(geom, P, t[ray])
+    e = network.encode_net(rbar, net).reshape(-1, net.d_in)
+    return e, geom.mu0 * l[ray], ray // D2, n.reshape(-1, D2).sum(axis=1)
+
+
+def forward_model_subpixel(M, w, pix, n_pix):
+    """Eq. 1 over the pixel's samples Phi_i: p_bar_i = (1/|Phi_i|) sum_j
+    w(r_ij) M(r_ij), 0 for a pixel none of whose rays meets the FOV."""
+    tot = np.bincount(pix, weights=w * M, minlength=len(n_pix))
+    return np.where(n_pix > 0, tot / np.maximum(n_pix, 1), 0.0)
+
+
 def forward_model(M, l, S: int, mu0: float):
     """Eq. 1 with w = mu0*l (Eq. 2) and |Phi| = S. M: [n, S]."""
     return mu0 * (l / S) * M.sum(axis=1)
@@ -47,11 +68,21 @@ def loss_and_grad(theta, geom, net, idx, proj, decide=None):
     decide="bf16" takes the ReLU decisions in BF16 (see
     network.relu_decisions_bf16); all values are FP64 either way."""
     S, B = geom.samples_per_ray, len(idx)
+    p = np.asarray(proj, np.float64)[np.asarray(idx)]
+    if getattr(geom, "subpixels", 0) > 0:
+        e, w, pix, n_pix = subpixel_model(geom, net, idx)
+        masks = network.relu_decisions_bf16(theta, net, e) if decide == "bf16" else None
+        M, cache = network.forward(theta, net, e, masks)
+        p_bar = forward_model_subpixel(M, w, pix, n_pix)
+        L = loss(p_bar, p)
+        # dL/dM_ij = (2/B) (p_bar_i - p_i) * w(r_ij) / |Phi_i|
+        dM = (2.0 / B) * (p_bar - p)[pix] * w / np.maximum(n_pix, 1)[pix]
+        g = network.backward(theta, net, cache, dM)
+        return dict(loss=L, p_bar=p_bar, grad=g, M=M, dM=dM, n_pix=n_pix)
     e, l = encoded_samples(geom, net, idx)
     masks = network.relu_decisions_bf16(theta, net, e) if decide == "bf16" else None
     M, cache = network.forward(theta, net, e, masks)
     M = M.reshape(B, S)
-    p = np.asarray(proj, np.float64)[np.asarray(idx)]
     p_bar = forward_model(M, l, S, geom.mu0)
     L = loss(p_bar, p)
     # dL/dM_ij = (2/B) (p_bar_i - p_i) * mu0 * l_i / S

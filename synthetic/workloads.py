@@ -50,6 +50,7 @@ class Geometry:
     t1: float = 1.0
     samples_per_ray: int = 32
     mu0: float = 1.0
+    subpixels: int = 0            # App. A model: D x D rays per pixel (0: one ray, S samples)
 
     @property
     def n_pixels(self) -> int:
@@ -165,7 +166,9 @@ def workload(c: int) -> Workload:
     network at scale, 5 serving (network of 3), 6 the paper's own network
     (GRFF encoding 2C = 256 with sigma_s = 0.5, sigma_t = 0.1, five Swish
     layers of 2C, linear output) on the geometry of 2, 7 the same network
-    at parity size (geometry of 1, 2C = 64, three layers)."""
+    at parity size (geometry of 1, 2C = 64, three layers), 8 and 9 the
+    networks of 6 and 7 with the paper's forward model (App. A: 2 x 2
+    sub-pixel rays per pixel, samples about half a pixel apart)."""
     if c == 1:
         k = np.arange(64, dtype=np.float64)
         g = parallel_geometry(64, 32, 32, math.pi * k / 64, k / 64, 32)
@@ -195,6 +198,16 @@ def workload(c: int) -> Workload:
         return replace(w, index=6, net=net,
                        name="parallel-beam 512 views 128x128, S=128, GRFF 2C=256 + 5x256 Swish, "
                             "B=65536")
+    if c == 8:
+        w = workload(6)
+        return replace(w, index=8, geom=replace(w.geom, subpixels=2),
+                       name="parallel-beam 512 views 128x128, App. A forward model (2x2 "
+                            "sub-pixel rays, spacing pixel/2), GRFF 2C=256 + 5x256 Swish, B=65536")
+    if c == 9:
+        w = workload(7)
+        return replace(w, index=9, geom=replace(w.geom, subpixels=2),
+                       name="parallel-beam 64 views 32x32, App. A forward model (2x2 sub-pixel "
+                            "rays), GRFF 2C=64 + 3x64 Swish, B=1024")
     if c == 7:
         w = workload(1)
         net = Net(0, 3, 64, "swish", "identity", "grff", 32, 0.1, 0.5, 6007)
