@@ -150,9 +150,10 @@ def oracle_rate(w, n_rays, seed=11):
     proj[idx] = oph.projections(wl.phantom(w), g, idx)
     th = wl.he_init(net, w.seeds["weights"])
     t0 = time.perf_counter()
-    ostep.train_step(th, np.zeros_like(th), np.zeros_like(th), 1, g, net, w.train, idx, proj)
+    out = ostep.train_step(th, np.zeros_like(th), np.zeros_like(th), 1, g, net, w.train, idx, proj)
     dt = time.perf_counter() - t0
-    return n_rays * g.samples_per_ray / dt, dt
+    samples = int(out["n_pix"].sum()) if "n_pix" in out else n_rays * g.samples_per_ray
+    return samples / dt, dt
 
 
 def cpu_baseline(w, n_rays=2048):
@@ -190,12 +191,12 @@ def run_reference(args):
     n_rays = 256
     for _ in range(args.warmup):
         oracle_rate(w, n_rays, seed=7)
-    rates, total = [], 0.0
+    samples, total = 0.0, 0.0
     for k in range(args.steps):
         r, dt = oracle_rate(w, n_rays, seed=100 + k)
-        rates.append(r)
+        samples += r * dt
         total += dt
-    value = args.steps * n_rays * w.geom.samples_per_ray / total
+    value = samples / total
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -408,9 +409,13 @@ def emit(args, w, results, ws):
         print(json.dumps({"metric": METRIC, "error": main["error"]}), flush=True)
         return
     pk, src = peaks()
-    value = ws * main["steps"] * B * S / main["dt"]
     prof = main["prof"]
     launches = prof.pop("total_launches", {}).get("launches")
+    counted = prof.pop("total_samples", {}).get("launches")
+    # samples per step: B S with one ray per pixel; counted by the library
+    # with the App. A model (a variable number per pixel)
+    S_step = counted / main["steps"] if g.subpixels and counted else B * S
+    value = ws * main["steps"] * S_step / main["dt"]
     kern = {k: v for k, v in prof.items()}
     top = max(kern, key=lambda k: kern[k]["ms"])
     tk = kern[top]
@@ -430,7 +435,7 @@ def emit(args, w, results, ws):
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = top
     roof["launches"] = tk["launches"]
-    per_launch = B * S * main["steps"] / max(1, tk["launches"])   # samples per launch
+    per_launch = S_step * main["steps"] / max(1, tk["launches"])   # samples per launch
     roof["traffic"] = (traffic_of(top, w.index, per_launch) if args.prec == "bf16" else None)
     roof["traffic_unit"] = "bytes per launch (DRAM read + write)"
     total_ms = sum(v["ms"] for v in kern.values())
@@ -439,13 +444,16 @@ def emit(args, w, results, ws):
             "ms_per_step": 1e3 * main["dt"] / main["steps"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": config(w, {"parallelism": f"replicas{ws}" if ws > 1 else "single GPU",
-                                 "prec": args.prec}),
+                                 "prec": args.prec, "samples_per_step": S_step,
+                                 **({"forward_model": f"App. A, {g.subpixels}x{g.subpixels} "
+                                                      "sub-pixel rays, samples per pixel vary"}
+                                    if g.subpixels else {})}),
             "tflops_algorithmic": value * algorithmic_flops_per_sample(net) / 1e12,
             "roofline": roof,
             "kernel_shares": {k: round(v["ms"] / total_ms, 4) for k, v in kern.items()},
             "clocks": main["clocks"], "gpu_launches": launches,
-            "e2e": {"value": main["e2e"], "unit": "samples/s", "h2d_bytes_per_step": 8 * B,
-                    "d2h_bytes_per_step": 4},
+            "e2e": {"value": main["e2e"] * S_step / (B * S), "unit": "samples/s",
+                    "h2d_bytes_per_step": 8 * B, "d2h_bytes_per_step": 4},
             "loss_last": main["loss"]}
     for key in ("equal_error", "serving"):
         extra = results.pop(key, None)
@@ -454,7 +462,7 @@ def emit(args, w, results, ws):
     for p, r in results.items():
         if p != args.prec:
             line[f"{p}_path"] = ({"error": r["error"]} if "error" in r else
-                                 {"value": ws * r["steps"] * B * S / r["dt"], "unit": "samples/s",
+                                 {"value": ws * r["steps"] * S_step / r["dt"], "unit": "samples/s",
                                   "ms_per_step": 1e3 * r["dt"] / r["steps"]})
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
@@ -473,10 +481,11 @@ def main():
     ap.add_argument("--rays", type=int, default=0,
                     help="rays per step (default: the workload's 65,536); smaller batches "
                          "are for profiler captures, not bench lines")
-    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[2, 3, 4, 6],
+    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[2, 3, 4, 6, 8],
                     help="training workload (default: the benchmark workload 2; 3 and 4 are "
                          "the cone-beam 6x256 and 8x512 networks, 6 the paper's GRFF + Swish "
-                         "network on the geometry of 2)")
+                         "network on the geometry of 2, 8 the same with the App. A forward "
+                         "model)")
     ap.add_argument("--recompute", type=int, default=0,
                     help="activation recomputation of the unfused BF16 path (0, 1, -1 auto)")
     ap.add_argument("--equal-error-steps", type=int, default=200,

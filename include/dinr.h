@@ -109,6 +109,17 @@ typedef struct {
   double t0, t1;                 /* time range used for normalisation */
   int samples_per_ray;           /* S, 1..4096 */
   double mu0;                    /* Eq. 2 scale, about the mean attenuation */
+  int subpixels;                 /* forward model of training and prediction:
+                                    0 (or 1 with the fixed S): one ray through
+                                    each pixel centre, samples_per_ray samples;
+                                    D >= 1: App. A: D x D rays to the centres
+                                    of the pixel's sub-pixels, each sampled at
+                                    the midpoints of ceil(l / spacing) equal
+                                    parts of its chord l, spacing = pixel pitch
+                                    back-projected through the rotation axis
+                                    (x SOD/SDD for a cone beam) / D, and
+                                    p_bar = (1/|Phi|) sum mu0 l M over all the
+                                    pixel's samples (|Phi| samples). 0..8 */
 } dinr_geometry;
 
 /* Network shape (App. B). */

@@ -33,7 +33,7 @@ class Geometry(C.Structure):
                 ("det_off_v", C.c_double), ("sod", C.c_double), ("sdd", C.c_double),
                 ("fov_r", C.c_double), ("fov_z0", C.c_double), ("fov_z1", C.c_double),
                 ("t0", C.c_double), ("t1", C.c_double), ("samples_per_ray", C.c_int),
-                ("mu0", C.c_double)]
+                ("mu0", C.c_double), ("subpixels", C.c_int)]
 
 
 class Net(C.Structure):

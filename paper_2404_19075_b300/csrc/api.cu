@@ -109,6 +109,7 @@ static int check_geometry(const dinr_geometry *g) {
   if (!(g->fov_z1 > g->fov_z0) || !(g->t1 > g->t0)) return 0;
   if (g->samples_per_ray < 1 || g->samples_per_ray > 4096) return 0;
   if (g->beam == DINR_BEAM_CONE && (!(g->sod > g->fov_r) || !(g->sdd > g->sod))) return 0;
+  if (g->subpixels < 0 || g->subpixels > 8) return 0;
   return 1;
 }
 
@@ -153,6 +154,13 @@ static dinr_status setup_geometry(dinr_ctx *c, const dinr_geometry *g, GeoDev *g
   d.zs = 2.0 / (g->fov_z1 - g->fov_z0);
   d.zb = -(g->fov_z0 + g->fov_z1) / (g->fov_z1 - g->fov_z0);
   d.S = g->samples_per_ray;
+  d.D = g->subpixels;
+  d.spacing = 0.0;
+  if (d.D > 0) {
+    double pitch = g->det_pitch_u < g->det_pitch_v ? g->det_pitch_u : g->det_pitch_v;
+    if (g->beam == DINR_BEAM_CONE) pitch *= g->sod / g->sdd;
+    d.spacing = pitch / d.D;
+  }
   d.mu0 = (float)g->mu0;
   d.view_cs = *cs_out;
   d.view_tbar = *tbar_out;
@@ -240,6 +248,14 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
   dinr_status s = setup_geometry(c, geom, &c->geo, &c->d_view_cs, &c->d_view_tbar,
                                  &c->d_view_t, st);
   if (s != DINR_OK) return create_fail(c, s);
+  if (c->geo.D > 0) {
+    // App. A: workspaces hold the most samples a pixel can have, D^2 rays of
+    // ceil(longest chord / spacing) samples (longest chord: the cylinder's
+    // diagonal)
+    const double R = geom->fov_r, hz = geom->fov_z1 - geom->fov_z0;
+    const double lmax = std::sqrt(4.0 * R * R + hz * hz);
+    c->S = c->geo.D * c->geo.D * ((int)std::ceil(lmax / c->geo.spacing) + 1);
+  }
   c->n_proj = c->geo.n_proj;
 
   bool ok = true;
@@ -654,6 +670,7 @@ dinr_status dinr_profile(dinr_ctx *c, int enable) {
     c->prof_names.clear();
     c->prof_used = 0;
     c->launches = 0;
+    c->samples_done = 0;
   }
   return DINR_OK;
 }
@@ -681,6 +698,8 @@ dinr_status dinr_profile_report(dinr_ctx *c, char *buf, size_t size) {
     out += line;
   }
   snprintf(line, sizeof(line), "total_launches %lld 0 0 0\n", c->launches);
+  out += line;
+  snprintf(line, sizeof(line), "total_samples %lld 0 0 0\n", c->samples_done);
   out += line;
   snprintf(buf, size, "%s", out.c_str());
   return DINR_OK;

@@ -23,6 +23,8 @@ struct GeoDev {
   double R, z0, z1;         // FOV cylinder
   double inv_R, zs, zb;     // x_bar = x * inv_R, z_bar = z * zs + zb
   int S;                    // samples per ray
+  int D;                    // App. A sub-pixel rays per pixel side (0: one ray, S samples)
+  double spacing;           // App. A sample spacing: back-projected pixel / D
   float mu0;
   const double2 *view_cs;   // (cos theta_m, sin theta_m)
   const double *view_tbar;  // 2 (T_m - t0) / (t1 - t0) - 1

@@ -56,9 +56,11 @@ struct dinr_ctx {
   void *tc = nullptr;
   // query server state (serve.cu)
   void *serve = nullptr;
+  void *subpix = nullptr;         // App. A sub-ray workspace (subpixel.cu)
 
   // per-kernel event timing (dinr_profile)
   bool prof = false;
+  long long samples_done = 0;  // network samples of training passes since profiling began
   std::vector<std::string> prof_names;
   std::vector<ProfRec> prof_recs;
   std::vector<cudaEvent_t> prof_pool;

@@ -10,7 +10,8 @@ enum SampleSource {
   kSrcTrainRays = 0,   // rays of projection indices (Sec. III decode)
   kSrcVirtualView = 1, // rays of a rows x cols detector at (theta, t)
   kSrcPoints = 2,      // explicit (t, z, y, x) points
-  kSrcGrid = 3         // regular grid at time t
+  kSrcGrid = 3,        // regular grid at time t
+  kSrcSubRays = 4      // samples of App. A sub-pixel rays (ragged; see subpixel.cuh)
 };
 
 struct SourceArgs {
@@ -27,6 +28,13 @@ struct SourceArgs {
   double glo[3], gstep[3];   // (x, y, z)
   int gdims[3];              // (nx, ny, nz)
   double gtbar;
+  // kSrcSubRays: sample q belongs to sub-ray owner[q], whose first sample is
+  // sfirst[k]; srec (FP64) / srec32 (FP32) hold per sub-ray the normalised
+  // time, the normalised first sample (z, y, x) and step (z, y, x), and l.
+  const int *owner;
+  const long long *sfirst;
+  const double *srec;
+  const float *srec32;
 };
 
 // The ray of ray slot r for each ray source kind.
@@ -47,6 +55,16 @@ __device__ __forceinline__ void source_coords(const GeoDev &g, const SourceArgs 
     c[0] = ray.tbar;
     sample_coords(g, ray, j, S, c[1], c[2], c[3]);
     *len = (float)ray.l;
+  } else if (s.kind == kSrcSubRays) {
+    const long long q = s.first + r;
+    const int k = s.owner[q];
+    const double jd = (double)(q - s.sfirst[k]);
+    const double *R = s.srec + 8 * (long long)k;
+    c[0] = R[0];
+    c[1] = fma(jd, R[4], R[1]);
+    c[2] = fma(jd, R[5], R[2]);
+    c[3] = fma(jd, R[6], R[3]);
+    *len = 1.0f;
   } else if (s.kind == kSrcPoints) {
     const float *p = s.points + 4 * (s.first + r);
     c[0] = (double)p[0] * s.t_scale + s.t_bias;

@@ -317,6 +317,7 @@ __global__ void k_out_segsum_f32(const float *zH, long long ld, int W, int act, 
     if (lane == 0) z_out[r * S + j] = z;
     sumM += out_f(z, out_act);
   }
+  if (!p_bar) return;  // outputs only (ragged forward models sum them elsewhere)
   float l = ray_l[r];
   float pb = mu0 * (l / S) * sumM;
   if (lane == 0) {

@@ -6,6 +6,7 @@
 // adds its gradient into the step's gradient in a fixed order; the loss is
 // normalised by the whole minibatch size (Eq. 5).
 #include "context.cuh"
+#include "subpixel.cuh"
 #include "tc.cuh"
 
 using namespace dinr;
@@ -46,8 +47,15 @@ static int dw_splits(long long rows, int M, int N) {
   return (int)(s < 1 ? 1 : s);
 }
 
+static dinr_status f32_alloc(dinr_ctx *c);
+
 dinr_status alloc_workspace(dinr_ctx *c) {
-  if (c->prec != DINR_PREC_FP32) return tc_alloc(c);
+  dinr_status s = c->prec != DINR_PREC_FP32 ? tc_alloc(c) : f32_alloc(c);
+  if (s != DINR_OK) return s;
+  return subpix_alloc(c);
+}
+
+static dinr_status f32_alloc(dinr_ctx *c) {
   long long ns = (long long)c->chunk_rays * c->S;
   long long nr = ns;  // point queries use one "ray" per sample
   auto grab = [&](float **p, long long n) -> bool {
@@ -74,6 +82,7 @@ dinr_status alloc_workspace(dinr_ctx *c) {
 
 void destroy_backend(dinr_ctx *c) {
   if (c->prec != DINR_PREC_FP32) tc_destroy(c);
+  subpix_free(c);
 }
 
 dinr_status backend_poll(dinr_ctx *c) {
@@ -201,11 +210,54 @@ static dinr_status f32_backward(dinr_ctx *c, long long ns, bool acc) {
   return DINR_OK;
 }
 
+// Per-sample outputs z_out of ns encoded samples (FP32 path).
+static dinr_status f32_outputs(dinr_ctx *c, long long ns) {
+  dinr_status s = f32_hidden(c, ns);
+  if (s != DINR_OK) return s;
+  launch_out_segsum_f32(zlast(c, ns), c->W, c->W, c->act, c->out_act,
+                        c->d_params + c->offW[c->H], c->d_params + c->offb[c->H], ns, 1, c->mu0,
+                        nullptr, nullptr, 1.0f, false, c->zout, nullptr, nullptr, nullptr, c->st);
+  CKL();
+  return DINR_OK;
+}
+
+// App. A forward model of nr pixels idx (FP32 path): sub-rays, features of
+// every sample, network, ragged forward model; with train also the loss
+// terms and dL/dz.
+static dinr_status f32_subpix_pass(dinr_ctx *c, const long long *idx, int nr, float inv_B,
+                                   bool train, float *p_bar, long long *ns_out) {
+  long long ns = 0;
+  dinr_status s = subpix_setup(c, idx, nr, train ? c->d_proj : nullptr, &ns);
+  if (s != DINR_OK) return s;
+  SourceArgs src = subpix_source(c);
+  {
+    ProfScope ps(c, "encode", 0.0, 4.0 * ns * c->ldE);
+    launch_encode_f32(c->geo, src, ns, 1, c->F, c->grff_c, c->d_grff_B, c->ldE, c->E, nullptr,
+                      nullptr, nullptr, c->st);
+    CKL();
+  }
+  s = f32_outputs(c, ns);
+  if (s != DINR_OK) return s;
+  *ns_out = ns;
+  return subpix_segsum(c, c->zout, nr, inv_B, train, p_bar, train ? c->sq : nullptr,
+                       train ? c->dz : nullptr);
+}
+
 static dinr_status f32_loss_grad(dinr_ctx *c, int n) {
   float inv_B = 1.0f / (float)n;
   for (int r0 = 0, pass = 0; r0 < n; r0 += c->chunk_rays, ++pass) {
     int nr = n - r0 < c->chunk_rays ? n - r0 : c->chunk_rays;
     long long ns = (long long)nr * c->S;
+    if (c->geo.D > 0) {
+      dinr_status s = f32_subpix_pass(c, c->d_idx + r0, nr, inv_B, true, c->pbar, &ns);
+      if (s != DINR_OK) return s;
+      launch_loss_sum(c->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
+      CKL();
+      if (c->prof) c->samples_done += ns;
+      s = f32_backward(c, ns, pass > 0);
+      if (s != DINR_OK) return s;
+      continue;
+    }
     SourceArgs src{};
     src.kind = kSrcTrainRays;
     src.idx = c->d_idx + r0;
@@ -224,7 +276,8 @@ static dinr_status f32_loss_grad(dinr_ctx *c, int n) {
     CKL();
     launch_loss_sum(c->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
     CKL();
-    s = f32_backward(c, ns, pass > 0);
+    if (c->prof) c->samples_done += ns;
+      s = f32_backward(c, ns, pass > 0);
     if (s != DINR_OK) return s;
   }
   return DINR_OK;
@@ -233,6 +286,15 @@ static dinr_status f32_loss_grad(dinr_ctx *c, int n) {
 // Forward model of ray (S > 0) or point (S = 1, l = 1) sources, in passes.
 static dinr_status f32_forward(dinr_ctx *c, const SourceArgs &src0, long long n_rays, int S,
                                float *out) {
+  if (src0.kind == kSrcTrainRays && c->geo.D > 0) {  // App. A model of minibatch pixels
+    for (long long r0 = 0; r0 < n_rays; r0 += c->chunk_rays) {
+      int nr = (int)(n_rays - r0 < c->chunk_rays ? n_rays - r0 : c->chunk_rays);
+      long long ns = 0;
+      dinr_status s = f32_subpix_pass(c, src0.idx + r0, nr, 1.0f, false, out + r0, &ns);
+      if (s != DINR_OK) return s;
+    }
+    return DINR_OK;
+  }
   long long per = (long long)c->chunk_rays * c->S / S;
   if (per < 1) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "S larger than the workspace");
   for (long long r0 = 0; r0 < n_rays; r0 += per) {

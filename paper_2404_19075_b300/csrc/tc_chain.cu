@@ -324,7 +324,8 @@ template <int F>
 __device__ __forceinline__ void tile_features(const ChainArgs &p, uint8_t *A, long long tile,
                                               long long smp, bool live, int r_in, int q,
                                               int half, int lane) {
-  const bool ray_src = p.src.kind == kSrcTrainRays || p.src.kind == kSrcVirtualView;
+  const bool ray_src = p.src.kind == kSrcTrainRays || p.src.kind == kSrcVirtualView ||
+                       p.src.kind == kSrcSubRays;
   // Normalised (t, z, y, x) in FP32. A ray is set up once in FP64 (chord,
   // normalised start point of its first sample and normalised step); its
   // samples are then start + j * step in FP32, whose rounding (about 1e-7)
@@ -333,8 +334,15 @@ __device__ __forceinline__ void tile_features(const ChainArgs &p, uint8_t *A, lo
   float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (ray_src) {
     const long long s0 = live ? smp : 0;
-    const long long r = s0 / p.S;
-    const int j = (int)(s0 - r * p.S);
+    long long r;
+    int j;
+    if (p.owner) {  // App. A: ragged rays
+      r = live ? p.owner[s0] : 0;
+      j = (int)(s0 - p.sfirst[r]);
+    } else {
+      r = s0 / p.S;
+      j = (int)(s0 - r * p.S);
+    }
     if (live) {
       // tbar, start (z, y, x), step (z, y, x), chord length
       const float4 a = ld_stream4(p.rays + 8 * r);

@@ -54,6 +54,8 @@ struct ChainArgs {
   float *ray_l, *ray_p;            // [n_rays]
   const float *rays;               // per-ray records [n_rays][8] (ray sources), see
                                    // launch_ray_records
+  const int *owner;                // App. A: ray of each sample (null: S samples per ray)
+  const long long *sfirst;         // App. A: first sample of each ray
   int act;                         // kActRelu or kActSwish
   uint32_t *masks[kChainMaxLayers];  // ReLU: bits of h_L, [samples][W/32] words
   __nv_bfloat16 *gact[kChainMaxLayers];  // Swish: derivative at z_L, [samples][W] BF16

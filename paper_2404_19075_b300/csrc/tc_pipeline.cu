@@ -10,6 +10,7 @@
 // the input gradients; wider layers run as N-tiled GEMMs, optionally with
 // activation recomputation (only checkpoint layers kept, the others
 // recomputed by the same forward GEMM in the backward).
+#include "subpixel.cuh"
 #include "tc.cuh"
 #include "tc_chain.cuh"
 #include "tc_gemm.cuh"
@@ -475,6 +476,11 @@ dinr_status chain(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S, b
     launch_ray_records(c->geo, src, n_rays, S, t->rec, t->ray_l, proj, a.ray_p, c->st);
     CKL();
     a.rays = t->rec;
+  } else if (src.kind == kSrcSubRays) {  // App. A records from subpix_setup
+    a.rays = src.srec32;
+    a.owner = src.owner;
+    a.sfirst = src.sfirst;
+    a.ray_l = nullptr;
   }
   double pw = (double)c->W * c->d_in + (double)(c->H - 1) * c->W * c->W + c->W;
   ProfScope ps(c, "tc_fwd_chain", 2.0 * ns * pw,
@@ -765,12 +771,39 @@ dinr_status tc_params_changed(dinr_ctx *c) {
   return DINR_OK;
 }
 
+// Outputs z_out of the samples of the last sub-ray setup (App. A): fused
+// chain or encode + forward GEMMs.
+static dinr_status subpix_outputs(dinr_ctx *c, long long ns, bool store_h) {
+  TcState *t = S_(c);
+  SourceArgs src = subpix_source(c);
+  if (chain_ok(c)) return chain(c, src, ns, 1, store_h, nullptr);
+  {
+    ProfScope ps(c, "encode", 0.0, 2.0 * ns * c->ldE);
+    launch_encode_bf16(c->geo, src, ns, 1, c->F, c->grff_c, c->d_grff_B, c->ldE, t->E, nullptr,
+                       nullptr, nullptr, c->st);
+    CKL();
+  }
+  return forward(c, ns);
+}
+
 dinr_status tc_loss_grad(dinr_ctx *c, int n) {
   TcState *t = S_(c);
   float inv_B = 1.0f / (float)n;
   for (int r0 = 0, pass = 0; r0 < n; r0 += c->chunk_rays, ++pass) {
     int nr = n - r0 < c->chunk_rays ? n - r0 : c->chunk_rays;
     long long ns = (long long)nr * c->S;
+    if (c->geo.D > 0) {
+      dinr_status s = subpix_setup(c, c->d_idx + r0, nr, c->d_proj, &ns);
+      if (s == DINR_OK) s = subpix_outputs(c, ns, true);
+      if (s == DINR_OK) s = subpix_segsum(c, t->zout, nr, inv_B, true, t->pbar, t->sq, t->dz);
+      if (s != DINR_OK) return s;
+      launch_loss_sum(t->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
+      CKL();
+      if (c->prof) c->samples_done += ns;
+      s = backward(c, ns, pass > 0);
+      if (s != DINR_OK) return s;
+      continue;
+    }
     SourceArgs src{};
     src.kind = kSrcTrainRays;
     src.idx = c->d_idx + r0;
@@ -792,7 +825,8 @@ dinr_status tc_loss_grad(dinr_ctx *c, int n) {
     CKL();
     launch_loss_sum(t->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
     CKL();
-    s = backward(c, ns, pass > 0);
+    if (c->prof) c->samples_done += ns;
+      s = backward(c, ns, pass > 0);
     if (s != DINR_OK) return s;
   }
   if (t->fp8) {
@@ -805,6 +839,17 @@ dinr_status tc_loss_grad(dinr_ctx *c, int n) {
 static dinr_status tc_forward(dinr_ctx *c, const SourceArgs &src0, long long n_rays, int S,
                               float *out) {
   TcState *t = S_(c);
+  if (src0.kind == kSrcTrainRays && c->geo.D > 0) {  // App. A model of minibatch pixels
+    for (long long r0 = 0; r0 < n_rays; r0 += c->chunk_rays) {
+      int nr = (int)(n_rays - r0 < c->chunk_rays ? n_rays - r0 : c->chunk_rays);
+      long long ns = 0;
+      dinr_status s = subpix_setup(c, src0.idx + r0, nr, nullptr, &ns);
+      if (s == DINR_OK) s = subpix_outputs(c, ns, false);
+      if (s == DINR_OK) s = subpix_segsum(c, t->zout, nr, 1.0f, false, out + r0, nullptr, nullptr);
+      if (s != DINR_OK) return s;
+    }
+    return DINR_OK;
+  }
   long long per = (long long)c->chunk_rays * c->S / S;
   if (per < 1) return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "S larger than the workspace");
   for (long long r0 = 0; r0 < n_rays; r0 += per) {

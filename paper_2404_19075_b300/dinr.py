@@ -59,7 +59,7 @@ def geometry_struct(g):
         g.det_cols, angle.ctypes.data_as(C.POINTER(C.c_double)),
         time.ctypes.data_as(C.POINTER(C.c_double)), g.det_pitch_u, g.det_pitch_v,
         g.det_off_u, g.det_off_v, g.sod, g.sdd, g.fov_r, g.fov_z0, g.fov_z1, g.t0, g.t1,
-        g.samples_per_ray, g.mu0)
+        g.samples_per_ray, g.mu0, getattr(g, "subpixels", 0))
     return s, (angle, time)
 
 
