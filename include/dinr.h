@@ -368,6 +368,14 @@ DINR_API dinr_status dinr_profile_report(dinr_ctx *ctx, char *buf, size_t size);
 /* Wait for all work of the context. */
 DINR_API dinr_status dinr_synchronize(dinr_ctx *ctx);
 
+/* Diagnostics: exercises the bounded waits of the tensor-core kernels
+ * without any fault. One warp waits on a barrier that nothing arrives on,
+ * through the same wait primitive and error-flag protocol as the persistent
+ * kernels but with a limit of limit_ns (1 ms .. 4 s) instead of 4 s; the
+ * kernel gives up, records the timeout and returns, and the call returns
+ * DINR_ERR_TIMEOUT as a real timeout would. The context stays usable. */
+DINR_API dinr_status dinr_selftest_timeout(dinr_ctx *ctx, int64_t limit_ns);
+
 /* Message of the last failure of this context (or of the last failed
  * creation when ctx is NULL). Never NULL. */
 DINR_API const char *dinr_last_error(const dinr_ctx *ctx);

@@ -77,6 +77,7 @@ PROTOTYPES = {
     "dinr_query": (C.c_int, [vp, vp, i64, vp]),
     "dinr_query_grid": (C.c_int, [vp, C.c_double, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.POINTER(C.c_int), vp]),
+    "dinr_selftest_timeout": (C.c_int, [vp, i64]),
     "dinr_export": (C.c_int, [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.POINTER(C.c_int), VOLUME_SINK, vp]),
     "dinr_set_params": (C.c_int, [vp, vp, C.c_int]),

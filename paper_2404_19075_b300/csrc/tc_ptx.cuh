@@ -70,17 +70,21 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
 // gave up) the thread sleeps in the barrier for at most kSleepNs.
 constexpr uint64_t kWaitNs = 4000000000ULL;
 constexpr uint32_t kSleepNs = 200000;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, int *err, int code,
+                                              uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (;;) {
     if (mbar_try_wait_sleep(bar, parity, kSleepNs)) return true;
     if (*(volatile int *)err != 0) return false;  // another role already gave up
-    if (globaltimer() - t0 > kWaitNs) {
+    if (globaltimer() - t0 > limit_ns) {
       atomicCAS(err, 0, code);
       return false;
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+  return mbar_wait_for(bar, parity, err, code, kWaitNs);
 }
 
 // mbar_wait for all 32 lanes of a warp with a warp-uniform result, so that

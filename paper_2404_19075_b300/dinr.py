@@ -194,6 +194,11 @@ class Dinr:
         self._c(_abi.lib().dinr_query_grid(self._h, float(t), lo_a, hi_a, d_a, _ptr(out)))
         return out.view(dims[2], dims[1], dims[0])
 
+    def selftest_timeout(self, limit_s=0.05):
+        """Make a kernel's bounded wait run out (see dinr_selftest_timeout);
+        raises DinrError with status TIMEOUT."""
+        self._c(_abi.lib().dinr_selftest_timeout(self._h, int(limit_s * 1e9)))
+
     def export(self, times, lo, hi, dims, sink):
         """4D export: sink(k, t, volume) for each time in order, volume a
         host float32 array [nz, ny, nx] valid during the call (copy it to
