@@ -120,6 +120,24 @@ __device__ __forceinline__ void st_stream16(void *p, uint4 v) {
                "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
 }
+// Swish derivatives of layer L in HBM, tile-interleaved so that a warp's 32
+// rows of one 16-byte column unit are 512 contiguous bytes (coalesced in
+// both chains): unit (row, chunk jc, unit c16) at
+// (((row / 128) * (W / 64) + jc) * 8 + c16) * 2048 + (row % 128) * 16.
+__device__ __forceinline__ uint8_t *gact_unit(const ChainArgs &p, int L, long long row, int jc,
+                                              int c16) {
+  return reinterpret_cast<uint8_t *>(p.gact[L]) +
+         ((((row >> 7) * (p.W / 64) + jc) * 8 + c16) << 11) + ((row & 127) << 4);
+}
+
+// ReLU bits of layer L in HBM, tile-interleaved the same way: the two
+// words of (row, 64-column chunk jc) at
+// ((row / 128) * (W / 64) + jc) * 256 + (row % 128) * 2, so that a warp's 32
+// rows are 256 contiguous bytes.
+__device__ __forceinline__ uint32_t *mask_unit(const ChainArgs &p, int L, long long row, int jc) {
+  return p.masks[L] + (((row >> 7) * (p.W / 64) + jc) << 8) + ((row & 127) << 1);
+}
+
 // Low / high BF16 half of a packed pair, as FP32.
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
@@ -457,10 +475,10 @@ __device__ __forceinline__ void swish_chunk(const ChainArgs &p, uint8_t *chunk, 
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, 4 * hh + u)) =
           make_uint4(wh[4 * u], wh[4 * u + 1], wh[4 * u + 2], wh[4 * u + 3]);
     if (live && p.gact[L]) {
-      uint8_t *gp = reinterpret_cast<uint8_t *>(p.gact[L] + row * p.W + c0);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        st_stream16(gp + 16 * u, make_uint4(wg[4 * u], wg[4 * u + 1], wg[4 * u + 2], wg[4 * u + 3]));
+        st_stream16(gact_unit(p, L, row, jc, 4 * hh + u),
+                    make_uint4(wg[4 * u], wg[4 * u + 1], wg[4 * u + 2], wg[4 * u + 3]));
     }
   }
 }
@@ -515,8 +533,7 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
     for (int c16 = 0; c16 < 8; ++c16)
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) =
           make_uint4(w[4 * c16], w[4 * c16 + 1], w[4 * c16 + 2], w[4 * c16 + 3]);
-    if (live && p.masks[L])
-      st_stream2(p.masks[L] + row * (p.W / 32) + 2 * jc, make_uint2(bits[0], bits[1]));
+    if (live && p.masks[L]) st_stream2(mask_unit(p, L, row, jc), make_uint2(bits[0], bits[1]));
   }
   fence_async_smem();
   __syncwarp();
@@ -568,13 +585,15 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
   const bool live = row < p.ns;
   const float dzr = live ? p.dz[row] : 0.0f;
   if constexpr (kAct == kActSwish) {
-    const uint8_t *grow = reinterpret_cast<const uint8_t *>(p.gact[p.H - 1] + (live ? row : 0) * p.W);
     for (int jc = half; jc < p.W / 64; jc += 2) {
       uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+      uint4 gq[8];  // the chunk's derivatives, all loads in flight together
+#pragma unroll
+      for (int c16 = 0; c16 < 8; ++c16)
+        gq[c16] = live ? ld_stream16(gact_unit(p, p.H - 1, row, jc, c16)) : make_uint4(0, 0, 0, 0);
 #pragma unroll
       for (int c16 = 0; c16 < 8; ++c16) {
-        const uint4 gq = live ? ld_stream16(grow + 128 * jc + 16 * c16) : make_uint4(0, 0, 0, 0);
-        const uint32_t gw[4] = {gq.x, gq.y, gq.z, gq.w};
+        const uint32_t gw[4] = {gq[c16].x, gq[c16].y, gq[c16].z, gq[c16].w};
         const float4 oa = ld_keep(p.w_out + 64 * jc + 8 * c16);
         const float4 ob = ld_keep(p.w_out + 64 * jc + 8 * c16 + 4);
         const float o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
@@ -588,9 +607,8 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
     store_chunks(maps, p, A, p.H - 1, tile, q, half, lane);
     return;
   }
-  const uint32_t *mrow = p.masks[p.H - 1] + (live ? row : 0) * (p.W / 32);
   for (int jc = half; jc < p.W / 64; jc += 2) {
-    const uint2 mb = live ? ld_stream2(mrow + 2 * jc) : make_uint2(0u, 0u);
+    const uint2 mb = live ? ld_stream2(mask_unit(p, p.H - 1, row, jc)) : make_uint2(0u, 0u);
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
 #pragma unroll
     for (int c16 = 0; c16 < 8; ++c16) {
@@ -616,11 +634,10 @@ __device__ bool bwd_epilogue_swish(const ChainMaps &maps, const ChainArgs &p, co
   const int r_in = q * 32 + lane;
   const long long row = tile * 128 + r_in;
   const bool live = row < p.ns;
-  const uint8_t *grow = reinterpret_cast<const uint8_t *>(p.gact[L - 1] + (live ? row : 0) * p.W);
   uint4 gq[8];
 #pragma unroll
   for (int c16 = 0; c16 < 8; ++c16)
-    gq[c16] = live && half < p.W / 64 ? ld_stream16(grow + 128 * half + 16 * c16)
+    gq[c16] = live && half < p.W / 64 ? ld_stream16(gact_unit(p, L - 1, row, half, c16))
                                       : make_uint4(0, 0, 0, 0);
   if (!warp_wait(&s.tfull[slot], tfull_phase & 1, p.err, 18)) return false;
   tc_fence_after();
@@ -628,11 +645,15 @@ __device__ bool bwd_epilogue_swish(const ChainMaps &maps, const ChainArgs &p, co
   __syncwarp();
   const uint32_t trow = tcol + ((uint32_t)(q * 32) << 16);
   uint8_t *A = s.A[slot];
+  // the next chunk's derivatives are requested before this chunk is
+  // processed, so their latency overlaps it
+  uint4 gn[8];
   for (int jc = half; jc < p.W / 64; jc += 2) {
-    if (jc != half) {
+    const bool more = jc + 2 < p.W / 64;
+    if (more) {
 #pragma unroll
       for (int c16 = 0; c16 < 8; ++c16)
-        gq[c16] = live ? ld_stream16(grow + 128 * jc + 16 * c16) : make_uint4(0, 0, 0, 0);
+        gn[c16] = live ? ld_stream16(gact_unit(p, L - 1, row, jc + 2, c16)) : make_uint4(0, 0, 0, 0);
     }
     float v[64];
     tmem_ld64(trow + 64 * jc, v);
@@ -647,6 +668,10 @@ __device__ bool bwd_epilogue_swish(const ChainMaps &maps, const ChainArgs &p, co
         w[e] = pack2(v[i] * bf_lo(gw[e]), v[i + 1] * bf_hi(gw[e]));
       }
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (more) {
+#pragma unroll
+      for (int c16 = 0; c16 < 8; ++c16) gq[c16] = gn[c16];
     }
   }
   store_chunks(maps, p, A, L - 1, tile, q, half, lane);
@@ -663,11 +688,11 @@ __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Sm
   const int r_in = q * 32 + lane;
   const long long row = tile * 128 + r_in;
   const bool live = row < p.ns;
-  const uint32_t *mrow = p.masks[L - 1] + (live ? row : 0) * (p.W / 32);
+
   uint2 mb[2] = {make_uint2(0u, 0u), make_uint2(0u, 0u)};
   if (live)  // before the wait: the ReLU bits of this warp's (at most two) chunks
     for (int k = 0; k < 2 && half + 2 * k < p.W / 64; ++k)
-      mb[k] = ld_stream2(mrow + 2 * (half + 2 * k));
+      mb[k] = ld_stream2(mask_unit(p, L - 1, row, half + 2 * k));
   if (!warp_wait(&s.tfull[slot], tfull_phase & 1, p.err, 18)) return false;
   tc_fence_after();
   if (lane == 0) bulk_wait_read();

@@ -57,8 +57,12 @@ struct ChainArgs {
   const int *owner;                // App. A: ray of each sample (null: S samples per ray)
   const long long *sfirst;         // App. A: first sample of each ray
   int act;                         // kActRelu or kActSwish
-  uint32_t *masks[kChainMaxLayers];  // ReLU: bits of h_L, [samples][W/32] words
-  __nv_bfloat16 *gact[kChainMaxLayers];  // Swish: derivative at z_L, [samples][W] BF16
+  // ReLU: bits of h_L, W/32 words per sample, tile-interleaved (see
+  // mask_unit in tc_chain.cu), ceil(samples / 128) * 128 * W / 32 words per layer
+  uint32_t *masks[kChainMaxLayers];
+  // Swish: derivative at z_L, BF16, tile-interleaved (see gact_unit in
+  // tc_chain.cu), ceil(samples / 128) * 128 * W values per layer
+  __nv_bfloat16 *gact[kChainMaxLayers];
   const float *proj;               // measured stack (training rays) or null
   // serving batches: per-tile work items (null for a single source)
   const WorkItem *items;

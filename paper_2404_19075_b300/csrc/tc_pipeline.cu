@@ -408,8 +408,8 @@ void set_act_buffers(dinr_ctx *c, ChainArgs &a, long long ns) {
   TcState *t = S_(c);
   a.act = c->act == DINR_ACT_SWISH ? kActSwish : kActRelu;
   for (int L = 0; L < c->H; ++L) {
-    if (t->masks) a.masks[L] = t->masks + (long long)L * ns * (c->W / 32);
-    if (t->G) a.gact[L] = t->G + (long long)L * ns * c->W;
+    if (t->masks) a.masks[L] = t->masks + (long long)L * ((ns + 127) / 128 * 128) * (c->W / 32);
+    if (t->G) a.gact[L] = t->G + (long long)L * ((ns + 127) / 128 * 128) * c->W;
   }
 }
 
@@ -705,8 +705,9 @@ dinr_status tc_alloc(dinr_ctx *c) {
   t->chain = chains_used(c);
   if (t->chain)
     ok = ok && grab((void **)&t->Dall, 2ull * ns * c->W * c->H) &&
-         (c->act == DINR_ACT_SWISH ? grab((void **)&t->G, 2ull * ns * c->W * c->H)
-                                   : grab((void **)&t->masks, 4ull * ns * (c->W / 32) * c->H)) &&
+         (c->act == DINR_ACT_SWISH ? grab((void **)&t->G, 2ull * ((ns + 127) / 128 * 128) * c->W * c->H)
+                                   : grab((void **)&t->masks,
+                                          4ull * ((ns + 127) / 128 * 128) * (c->W / 32) * c->H)) &&
          grab((void **)&t->rec, 32ull * ns);
   else
     ok = ok && grab((void **)&t->D0, 2ull * ns * c->W) && grab((void **)&t->D1, 2ull * ns * c->W);
