@@ -14,6 +14,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <cstring>
+
 namespace dinr {
 
 using namespace tc;
@@ -24,8 +26,11 @@ constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int kOnesBytes = 1024;
 
+constexpr int kStageBytes = 32 * 32 * 2;  // one warp's 32 x 32 BF16 output block
+
 struct Smem {
   uint8_t *a, *b, *ones;
+  uint8_t *stage;  // [8 epilogue warps][2] output blocks (stage_out)
   float *dot;  // [2 tile parities][2 halves][128 rows]
   uint64_t *full, *empty, *tfull, *tempty, *drain, *dotbar;
   uint32_t *tslot;
@@ -36,7 +41,8 @@ __device__ __forceinline__ Smem carve(uint8_t *base, const TcGemmArgs &p) {
   s.a = base;
   s.b = base + (size_t)p.stages * p.a_bytes;
   s.ones = s.b + (size_t)p.stages * p.b_bytes;
-  s.dot = reinterpret_cast<float *>(s.ones + kOnesBytes);
+  s.stage = s.ones + kOnesBytes;
+  s.dot = reinterpret_cast<float *>(s.stage + (p.stage_out ? kEpiWarps * 2 * kStageBytes : 0));
   s.full = reinterpret_cast<uint64_t *>(s.dot + 2 * 2 * 128);
   s.empty = s.full + p.stages;
   s.tfull = s.empty + p.stages;
@@ -190,14 +196,15 @@ __device__ __forceinline__ float swish_grad(float z) {
   return s * (1.0f + z * (1.0f - s));
 }
 
-__device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
+__device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
+                         const CUtensorMap *tout) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int q = warp & 3;              // TMEM lane quadrant this warp may access
   const int half = (warp - 2) / 4;     // which alternate 32-column chunks
   const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
   const int n_tiles = p.m_tiles * n_tn(p) * p.splits;
   const int n_chunks = (p.N + 31) / 32;
-  uint32_t lt = 0;
+  uint32_t lt = 0, staged = 0;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
     int mt, nt, sp, nk;
     long long k0;
@@ -288,7 +295,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
             }
           }
         }
-        if (p.epi == kTcFwd || p.epi == kTcDx) {
+        if ((p.epi == kTcFwd || p.epi == kTcDx) && !p.stage_out) {
           if (c0 + 32 <= p.n_store) {
             uint4 *o = reinterpret_cast<uint4 *>(p.out + (long long)row * p.ldo + c0);
 #pragma unroll
@@ -301,9 +308,30 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
             for (int i = 0; i < 32 && c0 + i < p.n_store; ++i)
               p.out[(long long)row * p.ldo + c0 + i] = __float2bfloat16_rn(v[i]);
           }
-        } else {
+        } else if (p.epi == kTcDw) {
           float *o = p.part + ((long long)sp * p.M + row) * p.part_ld + c0;
           for (int i = 0; i < 32 && c0 + i < p.n_store; ++i) o[i] = v[i];
+        }
+      }
+      if (p.stage_out) {
+        // the warp's 32 x 32 block through shared memory and one TMA store
+        // (rows past M are clipped by the tensor map)
+        uint8_t *stg = s.stage + (size_t)((warp - 2) * 2 + (staged & 1)) * kStageBytes;
+        ++staged;
+        if (lane == 0) bulk_wait_read1();  // this buffer's store of two chunks ago has read it
+        __syncwarp();
+        uint4 *o = reinterpret_cast<uint4 *>(stg + lane * 64);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          o[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]), pack_bf16(v[8 * j + 2], v[8 * j + 3]),
+                            pack_bf16(v[8 * j + 4], v[8 * j + 5]),
+                            pack_bf16(v[8 * j + 6], v[8 * j + 7]));
+        fence_async_smem();
+        __syncwarp();
+        const int row0 = mt * BM + q * 32;
+        if (lane == 0 && row0 < p.M) {
+          tma_store_2d(tout, stg, c0, row0);
+          bulk_commit();
         }
       }
       if (p.epi == kTcDx) {
@@ -342,11 +370,13 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
     __syncwarp();
     if (lane == 0) mbar_arrive(&s.tempty[ab]);
   }
+  if (p.stage_out && lane == 0) bulk_wait_all();  // stores done before the CTA exits
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-              const TcGemmArgs p) {
+              const __grid_constant__ CUtensorMap tout, const TcGemmArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -385,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) mma_issuer(p, s, tbase);
   } else {
-    epilogue(p, s, tbase);
+    epilogue(p, s, tbase, &tout);
   }
   tc_fence_before();
   __syncthreads();
@@ -437,13 +467,30 @@ bool make_tmap_u8(CUtensorMap *tm, const void *ptr, long long rows, long long co
   return r == CUDA_SUCCESS;
 }
 
-int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, TcGemmArgs a, int num_sms,
-                   cudaStream_t st) {
+bool make_tmap_bf16_plain(CUtensorMap *tm, const void *ptr, long long rows, long long cols,
+                          long long ld, int box_cols, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap *tout,
+                   TcGemmArgs a, int num_sms, cudaStream_t st) {
+  if (a.stage_out && (!tout || a.epi == kTcDw || a.n_store % 32 != 0))
+    return (int)cudaErrorInvalidValue;
   if (a.fp8 && (a.epi != kTcFwd || a.a_mn || a.b_mn || a.with_db))
     return (int)cudaErrorInvalidValue;
   a.a_bytes = BM * BK * 2;  // 128 rows x 128 bytes, or 2 MN-major boxes of 64 x 128 bytes
   a.b_bytes = a.b_mn ? ((a.N + 63) / 64) * 8192 : a.N * BK * 2;
-  const int fixed = kOnesBytes + 2048 /*dot buffer*/ + 1024 /*alignment*/ + 256 /*barriers*/;
+  const int fixed = kOnesBytes + 2048 /*dot buffer*/ + 1024 /*alignment*/ + 256 /*barriers*/ +
+                    (a.stage_out ? kEpiWarps * 2 * kStageBytes : 0);
   const int budget = 220 * 1024;
   int stages = (budget - fixed) / (a.a_bytes + a.b_bytes);
   a.stages = stages > 8 ? 8 : stages;
@@ -454,7 +501,9 @@ int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, TcGemmArgs a, i
   if (e != cudaSuccess) return (int)e;
   int tiles = a.m_tiles * (a.n_tn > 1 ? a.n_tn : 1) * a.splits;
   int grid = tiles < num_sms ? tiles : num_sms;
-  k_tc_gemm<<<grid, kThreads, smem, st>>>(ta, tb, a);
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  k_tc_gemm<<<grid, kThreads, smem, st>>>(ta, tb, tout ? *tout : none, a);
   return (int)cudaGetLastError();
 }
 

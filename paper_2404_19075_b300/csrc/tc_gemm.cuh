@@ -61,6 +61,10 @@ struct TcGemmArgs {
   uint8_t *out8;
   long long ldo8;
   unsigned int *amax;
+  // kTcFwd / kTcDx: write out through shared memory and TMA stores (a map
+  // of out with box {32, 32}, no swizzle, passed to launch_tc_gemm), so
+  // that every HBM write is a contiguous run; otherwise per-row stores.
+  int stage_out;
   // launch geometry (filled by the launcher)
   int stages, a_bytes, b_bytes;
   int *err;              // device flag: nonzero when a bounded wait gave up
@@ -74,8 +78,13 @@ bool make_tmap_bf16(CUtensorMap *tm, const void *ptr, long long rows, long long 
 bool make_tmap_u8(CUtensorMap *tm, const void *ptr, long long rows, long long cols, long long ld,
                   int box_rows);
 
-// Launches over min(tiles, SMs) persistent CTAs. Returns a cudaError_t.
-int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, TcGemmArgs a, int num_sms,
-                   cudaStream_t st);
+// 2D BF16 tensor map with box {box_cols, box_rows} and no swizzle.
+bool make_tmap_bf16_plain(CUtensorMap *tm, const void *ptr, long long rows, long long cols,
+                          long long ld, int box_cols, int box_rows);
+
+// Launches over min(tiles, SMs) persistent CTAs. tout: the map of out for
+// stage_out (else null). Returns a cudaError_t.
+int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap *tout,
+                   TcGemmArgs a, int num_sms, cudaStream_t st);
 
 }  // namespace dinr

@@ -252,7 +252,12 @@ dinr_status gemm(dinr_ctx *c, const char *name, double flops, double bytes, TcGe
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "tensor map encoding failed (%s)", name);
   a.err = S_(c)->err;
   ProfScope ps(c, name, flops, bytes);
-  int e = launch_tc_gemm(ta, tb, a, S_(c)->num_sms, c->st);
+  // forward and input-gradient outputs go out through staged TMA stores
+  CUtensorMap to;
+  const bool staged = a.epi != kTcDw && a.out && a.n_store % 32 == 0 &&
+                      make_tmap_bf16_plain(&to, a.out, a.M, a.n_store, a.ldo, 32, 32);
+  a.stage_out = staged ? 1 : 0;
+  int e = launch_tc_gemm(ta, tb, staged ? &to : nullptr, a, S_(c)->num_sms, c->st);
   ++c->launches;
   if (e != 0)
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "%s launch: %s", name,
@@ -305,7 +310,12 @@ dinr_status gemm8(dinr_ctx *c, const char *name, double flops, double bytes, TcG
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "tensor map encoding failed (%s)", name);
   a.err = S_(c)->err;
   ProfScope ps(c, name, flops, bytes);
-  int e = launch_tc_gemm(ta, tb, a, S_(c)->num_sms, c->st);
+  // forward and input-gradient outputs go out through staged TMA stores
+  CUtensorMap to;
+  const bool staged = a.epi != kTcDw && a.out && a.n_store % 32 == 0 &&
+                      make_tmap_bf16_plain(&to, a.out, a.M, a.n_store, a.ldo, 32, 32);
+  a.stage_out = staged ? 1 : 0;
+  int e = launch_tc_gemm(ta, tb, staged ? &to : nullptr, a, S_(c)->num_sms, c->st);
   ++c->launches;
   if (e != 0)
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "%s launch: %s", name,
