@@ -48,12 +48,30 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FM
 # the launch; 1,048,576-sample case of the benchmark workload, summarised in
 # profiles/). Valid only for the kernel source the counters were taken on:
 # a different source hash reports traffic as null.
-TRAFFIC = {"tc_fwd_chain": {"bytes_per_sample": 3.019e9 / 1048576, "bf16_workload": 2,
+# Either bytes per sample of every launch, or (for kernels whose bytes per
+# launch vary by layer) the measured DRAM bytes over the algorithmic bytes of
+# the captured launch, applied to each launch's algorithmic bytes.
+TRAFFIC = {"tc_fwd_chain": {"bytes_per_sample": (7.346944e6 + 3.011579e9) / 1048576,
+                            "bf16_workload": 2,
                             "source": "paper_2404_19075_b300/csrc/tc_chain.cu",
-                            "sha256_16": "95c5ed760537fcb2"}}
+                            "sha256_16": "f3d8542e5a1b0eaf"},
+           "tc_bwd_chain": {"bytes_per_sample": (175.909632e6 + 2.624694e9) / 1048576,
+                            "bf16_workload": 2,
+                            "source": "paper_2404_19075_b300/csrc/tc_chain.cu",
+                            "sha256_16": "f3d8542e5a1b0eaf"},
+           "tc_dw": {"ratio_to_algorithmic": (1.075681e9 + 6.929408e6) / (2 * 1048576 * 512 * 2),
+                     "bf16_workload": 2,
+                     "source": "paper_2404_19075_b300/csrc/tc_gemm.cu",
+                     "sha256_16": "2aa066c32de06e24"}}
+
+# Kernels bound by HBM bandwidth (their roofline is GB/s of algorithmic
+# bytes); the others are bound by the tensor pipe.
+HBM_BOUND = {"tc_dw", "dw_out", "encode"}
 
 
-def traffic_of(kernel, workload, samples):
+def traffic_of(kernel, workload, samples, alg_bytes):
+    """DRAM bytes of one launch from the recorded counters, or None when
+    there are none for this kernel and workload or its source has changed."""
     import hashlib
     t = TRAFFIC.get(kernel)
     if not t or t["bf16_workload"] != workload:
@@ -61,7 +79,36 @@ def traffic_of(kernel, workload, samples):
     with open(os.path.join(ROOT, t["source"]), "rb") as f:
         if hashlib.sha256(f.read()).hexdigest()[:16] != t["sha256_16"]:
             return None
-    return t["bytes_per_sample"] * samples
+    if "bytes_per_sample" in t:
+        return t["bytes_per_sample"] * samples
+    return t["ratio_to_algorithmic"] * alg_bytes
+
+
+def roofline_of(name, k, pk, src, prec, workload, samples_per_launch):
+    """Roofline entry of one profiled kernel (k: launches, ms, flops, bytes
+    summed over its launches)."""
+    t = k["ms"] / k["launches"] / 1e3                       # seconds per launch
+    if name in HBM_BOUND:
+        ach = k["bytes"] / k["launches"] / t / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+             "peak_source": f"hbm_gbs ({src})"}
+    elif prec == "bf16" or prec == "fp8":
+        ach = k["flops"] / k["launches"] / t / 1e12
+        peak = pk["bf16_tflops_sustained"] * (2 if prec == "fp8" else 1)
+        r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": ("2 x " if prec == "fp8" else "") + f"bf16_tflops_sustained ({src})"}
+    else:
+        ach = k["flops"] / k["launches"] / t / 1e12
+        r = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+    r["frac"] = r["achieved"] / r["peak"]
+    r["kernel"] = name
+    r["launches"] = k["launches"]
+    r["ms_per_launch"] = 1e3 * t
+    r["traffic"] = (traffic_of(name, workload, samples_per_launch, k["bytes"] / k["launches"])
+                    if prec != "fp32" else None)
+    r["traffic_unit"] = "bytes per launch (DRAM read + write)"
+    return r
 
 
 def peaks():
@@ -419,25 +466,11 @@ def emit(args, w, results, ws):
     kern = {k: v for k, v in prof.items()}
     top = max(kern, key=lambda k: kern[k]["ms"])
     tk = kern[top]
-    if args.prec == "fp8":
-        achieved = tk["flops"] / (tk["ms"] / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": 2 * pk["bf16_tflops_sustained"],
-                "unit": "TFLOP/s",
-                "peak_source": f"2 x bf16_tflops_sustained ({src}; dense FP8 is twice BF16)"}
-    elif args.prec == "bf16":
-        achieved = tk["flops"] / (tk["ms"] / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops_sustained"],
-                "unit": "TFLOP/s", "peak_source": f"bf16_tflops_sustained ({src})"}
-    else:
-        achieved = tk["flops"] / (tk["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = top
-    roof["launches"] = tk["launches"]
     per_launch = S_step * main["steps"] / max(1, tk["launches"])   # samples per launch
-    roof["traffic"] = (traffic_of(top, w.index, per_launch) if args.prec == "bf16" else None)
-    roof["traffic_unit"] = "bytes per launch (DRAM read + write)"
+    roof = roofline_of(top, tk, pk, src, args.prec, w.index, per_launch)
+    major = {name: roofline_of(name, k, pk, src, args.prec, w.index,
+                               S_step * main["steps"] / max(1, k["launches"]))
+             for name, k in kern.items() if k["ms"] >= 0.1 * tk["ms"] and k["launches"] > 0}
     total_ms = sum(v["ms"] for v in kern.values())
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,
             "steps": main["steps"], "warmup": args.warmup,
@@ -450,6 +483,7 @@ def emit(args, w, results, ws):
                                     if g.subpixels else {})}),
             "tflops_algorithmic": value * algorithmic_flops_per_sample(net) / 1e12,
             "roofline": roof,
+            "rooflines": major,
             "kernel_shares": {k: round(v["ms"] / total_ms, 4) for k, v in kern.items()},
             "clocks": main["clocks"], "gpu_launches": launches,
             "e2e": {"value": main["e2e"] * S_step / (B * S), "unit": "samples/s",

@@ -417,8 +417,37 @@ __global__ void k_colsum(const float *X, long long ld, int C, long long rows, co
     part[(long long)z * C + c] = acc + blk;
   }
 }
+// One column (e.g. the output bias gradient sum of dz): all 256 threads of a
+// block share the rows of its split (strided), then a fixed shared-memory
+// tree adds the thread sums.
+__global__ void __launch_bounds__(256)
+    k_colsum1(const float *X, long long ld, long long rows, const float *w, int apply_act,
+              int act, int splits, float *part) {
+  __shared__ float red[256];
+  const int z = blockIdx.x;
+  const long long per = (rows + splits - 1) / splits;
+  const long long r0 = z * per, r1 = r0 + per < rows ? r0 + per : rows;
+  float acc = 0.0f;
+  for (long long r = r0 + threadIdx.x; r < r1; r += 256) {
+    float x = X[r * ld];
+    if (apply_act) x = act_f(x, act);
+    acc += w ? w[r] * x : x;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[z] = red[0];
+}
+
 void launch_colsum(const float *X, long long ld, int C, long long rows, const float *w,
                    bool apply_act, int act, int splits, float *part, cudaStream_t st) {
+  if (C == 1) {
+    k_colsum1<<<splits, 256, 0, st>>>(X, ld, rows, w, apply_act ? 1 : 0, act, splits, part);
+    return;
+  }
   dim3 grid(ceil_div(C, 256), splits);
   k_colsum<<<grid, 256, 0, st>>>(X, ld, C, rows, w, apply_act ? 1 : 0, act, splits, part);
 }
