@@ -76,6 +76,23 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) {
   return *reinterpret_cast<float2 *>(&d);
 }
 
+// Packed FP32 multiply and fused multiply-add of two pairs.
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<uint64_t *>(&a)), "l"(*reinterpret_cast<uint64_t *>(&b)));
+  return *reinterpret_cast<float2 *>(&d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<uint64_t *>(&a)), "l"(*reinterpret_cast<uint64_t *>(&b)),
+        "l"(*reinterpret_cast<uint64_t *>(&c)));
+  return *reinterpret_cast<float2 *>(&d);
+}
+
 // BF16 pair (lo, hi) of max(x, 0), rounded to nearest even.
 __device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
   uint32_t d;
@@ -142,16 +159,25 @@ __device__ __forceinline__ uint32_t *mask_unit(const ChainArgs &p, int L, long l
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-// Swish z sigmoid(z) and its derivative sigmoid(z)(1 + z(1 - sigmoid(z))),
-// with sigmoid(z) = 1 / (1 + 2^(-z log2 e)) from the hardware exp2 and
-// reciprocal (relative error about 2^-22 for every z; a tanh-based sigmoid
-// loses relative accuracy for negative z, where 1/2 + tanh/2 cancels).
-__device__ __forceinline__ void swish_fg(float z, float &h, float &g) {
-  float e, sg;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-1.4426950408889634f * z));
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sg) : "f"(1.0f + e));
-  h = z * sg;
-  g = sg * fmaf(z, 1.0f - sg, 1.0f);
+// Swish h = z sigmoid(z) and its derivative g = sigmoid(z)(1 + z(1 - sigmoid(z)))
+// for a pair, in packed FP32, with sigmoid(z) = 1 / (1 + 2^(-z log2 e)) from
+// the hardware exp2 and reciprocal (relative error about 2^-22 for every z;
+// a tanh-based sigmoid loses relative accuracy for negative z, where
+// 1/2 + tanh/2 cancels). g is formed as s + h (1 - s); h and g are returned
+// as BF16 pairs, h also in FP32.
+__device__ __forceinline__ void swish_pair(float2 z, float2 &h, uint32_t &wh, uint32_t &wg) {
+  const float2 t = mul2(z, make_float2(-1.4426950408889634f, -1.4426950408889634f));
+  float2 e, sg;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(t.x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(t.y));
+  const float2 d = add2(e, make_float2(1.0f, 1.0f));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sg.x) : "f"(d.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sg.y) : "f"(d.y));
+  h = mul2(z, sg);
+  const float2 u = fma2(sg, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+  const float2 g = fma2(h, u, sg);
+  wh = pack2(h.x, h.y);
+  wg = pack2(g.x, g.y);
 }
 
 __device__ __forceinline__ void st_stream2(uint32_t *p, uint2 v) {
@@ -160,11 +186,13 @@ __device__ __forceinline__ void st_stream2(uint32_t *p, uint2 v) {
 }
 
 // ReLU bits. Of the 32 columns of a mask word, the pair (2k, 2k+1) sits at
-// bits 15-k and 31-k, so that one integer add flags both halves of a packed
-// BF16 pair: for non-negative halves (sign cleared), adding 0x7FFF sets bit
-// 15 of a half exactly when the half is nonzero, with no carry out of it.
+// bits 15-k and 31-k. A packed BF16 compare against zero gives 0xFFFF in
+// each half that is > 0, so one AND with the pair's two bit positions picks
+// its flags with no shift.
 __device__ __forceinline__ uint32_t pair_flags(uint32_t w, int k) {
-  return (((w & 0x7FFF7FFFu) + 0x7FFF7FFFu) & 0x80008000u) >> k;
+  uint32_t m;
+  asm("set.gt.u32.bf16x2 %0, %1, %2;" : "=r"(m) : "r"(w), "r"(0u));
+  return m & (0x80008000u >> k);
 }
 // 0xFFFF in each half of a BF16 pair whose bit is set in mask word m (pair k).
 __device__ __forceinline__ uint32_t pair_mask(uint32_t m, int k) {
@@ -433,53 +461,73 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
   }
 }
 
-// Swish part of the forward epilogue for one 64-column chunk: h = swish(z)
-// into the tile buffer (32 columns at a time), the derivative g into
-// gact[L] (the backward's factor in place of the ReLU mask), and on the last
-// layer the output dot product.
-__device__ __forceinline__ void swish_chunk(const ChainArgs &p, uint8_t *chunk, int jc, int L,
-                                            uint32_t trow, int r_in, long long row, bool live,
+// Swish part of the forward epilogue for the 32 columns c0 .. c0 + 31 whose
+// accumulators are in r: h = swish(z) into the tile buffer, the derivative
+// g into gact[L] (the backward's factor in place of the ReLU mask), and on
+// the last layer the output dot product.
+__device__ __forceinline__ void swish_group(const ChainArgs &p, uint8_t *A, int L, int c0,
+                                            const uint32_t (&r)[32], int r_in, uint8_t *gbase,
                                             bool last, float &dot) {
-  const float *bias = p.bias[L];
+  const float *bias = p.bias[L] + c0;
+  float4 bb[8];
 #pragma unroll
-  for (int hh = 0; hh < 2; ++hh) {
-    const int c0 = 64 * jc + 32 * hh;
-    float4 bb[8];
+  for (int i4 = 0; i4 < 8; ++i4) bb[i4] = ld_keep(bias + 4 * i4);
+  uint32_t wh[16], wg[16];
 #pragma unroll
-    for (int i4 = 0; i4 < 8; ++i4) bb[i4] = ld_keep(bias + c0 + 4 * i4);
-    float v[32];
-    tmem_ld32(trow + c0, v);
-    uint32_t wh[16], wg[16];
-#pragma unroll
-    for (int i4 = 0; i4 < 8; ++i4) {
-      const float4 b = bb[i4];
-      const float z[4] = {v[4 * i4] + b.x, v[4 * i4 + 1] + b.y, v[4 * i4 + 2] + b.z,
-                          v[4 * i4 + 3] + b.w};
-      float h[4], g[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) swish_fg(z[e], h[e], g[e]);
-      wh[2 * i4] = pack2(h[0], h[1]);
-      wh[2 * i4 + 1] = pack2(h[2], h[3]);
-      wg[2 * i4] = pack2(g[0], g[1]);
-      wg[2 * i4 + 1] = pack2(g[2], g[3]);
-      if (last) {
-        const float4 o = ld_keep(p.w_out + c0 + 4 * i4);
-        dot = fmaf(h[0], o.x, dot);
-        dot = fmaf(h[1], o.y, dot);
-        dot = fmaf(h[2], o.z, dot);
-        dot = fmaf(h[3], o.w, dot);
-      }
+  for (int i4 = 0; i4 < 8; ++i4) {
+    const float4 b = bb[i4];
+    const float2 z0 = add2(make_float2(__uint_as_float(r[4 * i4]), __uint_as_float(r[4 * i4 + 1])),
+                           make_float2(b.x, b.y));
+    const float2 z1 = add2(make_float2(__uint_as_float(r[4 * i4 + 2]),
+                                       __uint_as_float(r[4 * i4 + 3])),
+                           make_float2(b.z, b.w));
+    float2 h0, h1;
+    swish_pair(z0, h0, wh[2 * i4], wg[2 * i4]);
+    swish_pair(z1, h1, wh[2 * i4 + 1], wg[2 * i4 + 1]);
+    if (last) {
+      const float4 o = ld_keep(p.w_out + c0 + 4 * i4);
+      dot = fmaf(h0.x, o.x, dot);
+      dot = fmaf(h0.y, o.y, dot);
+      dot = fmaf(h1.x, o.z, dot);
+      dot = fmaf(h1.y, o.w, dot);
     }
+  }
+  const int jc = c0 >> 6, hh = (c0 >> 5) & 1;
+  uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    *reinterpret_cast<uint4 *>(chunk + swz(r_in, 4 * hh + u)) =
+        make_uint4(wh[4 * u], wh[4 * u + 1], wh[4 * u + 2], wh[4 * u + 3]);
+  if (gbase) {
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      *reinterpret_cast<uint4 *>(chunk + swz(r_in, 4 * hh + u)) =
-          make_uint4(wh[4 * u], wh[4 * u + 1], wh[4 * u + 2], wh[4 * u + 3]);
-    if (live && p.gact[L]) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        st_stream16(gact_unit(p, L, row, jc, 4 * hh + u),
-                    make_uint4(wg[4 * u], wg[4 * u + 1], wg[4 * u + 2], wg[4 * u + 3]));
-    }
+      st_stream16(gbase + ((size_t)(jc * 8 + 4 * hh + u) << 11),
+                  make_uint4(wg[4 * u], wg[4 * u + 1], wg[4 * u + 2], wg[4 * u + 3]));
+  }
+}
+
+// Swish epilogue of layer L over this warp's 32-column groups (columns
+// 64 (half + 2 m) + 32 hh). The TMEM load of the next group is in flight
+// while the current one is processed.
+__device__ __forceinline__ void swish_layer(const ChainArgs &p, uint8_t *A, int L,
+                                            uint32_t trow, int r_in, long long row, bool live,
+                                            bool last, int half, float &dot) {
+  const int ng = 2 * ((p.W / 64 - half + 1) / 2);
+  if (ng == 0) return;
+  // gact_unit(row, 0, 0) of layer L; unit (jc, c16) is 2048 (8 jc + c16) further
+  uint8_t *gbase = live && p.gact[L] ? gact_unit(p, L, row, 0, 0) : nullptr;
+  auto col = [&](int g) { return 64 * (half + 2 * (g >> 1)) + 32 * (g & 1); };
+  uint32_t ra[32], rb[32];
+  tmem_ld32_issue(trow + col(0), ra);
+  tmem_wait_ld32(ra);
+  for (int g = 0; g < ng; g += 2) {
+    tmem_ld32_issue(trow + col(g + 1), rb);
+    swish_group(p, A, L, col(g), ra, r_in, gbase, last, dot);
+    tmem_wait_ld32(rb);
+    const bool more = g + 2 < ng;
+    if (more) tmem_ld32_issue(trow + col(g + 2), ra);
+    swish_group(p, A, L, col(g + 1), rb, r_in, gbase, last, dot);
+    if (more) tmem_wait_ld32(ra);
   }
 }
 
@@ -498,11 +546,8 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
   const float *bias = p.bias[L];
   uint8_t *A = s.A[slot];
   float dot = 0.0f;
-  for (int jc = half; jc < p.W / 64; jc += 2) {
-    if constexpr (kAct == kActSwish) {
-      swish_chunk(p, A + (size_t)jc * kChunkBytes, jc, L, trow, r_in, row, live, last, dot);
-      continue;
-    }
+  if constexpr (kAct == kActSwish) swish_layer(p, A, L, trow, r_in, row, live, last, half, dot);
+  for (int jc = half; kAct != kActSwish && jc < p.W / 64; jc += 2) {
     // bias of the chunk first, so that its load overlaps the TMEM load
     float4 bb[16];
 #pragma unroll
