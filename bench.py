@@ -45,24 +45,26 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FM
 
 # DRAM bytes per sample of the fused kernels, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the launch / samples of
-# the launch; 1,048,576-sample case of the benchmark workload, summarised in
-# profiles/). Valid only for the kernel source the counters were taken on:
-# a different source hash reports traffic as null.
+# the launch; 1,048,576-sample cases of the parallel-beam workloads 2 (ReLU,
+# octave encoding) and 6 (GRFF + Swish), summarised in profiles/). Valid only
+# for the kernel source the counters were taken on: a different source hash
+# reports traffic as null.
 # Either bytes per sample of every launch, or (for kernels whose bytes per
 # launch vary by layer) the measured DRAM bytes over the algorithmic bytes of
 # the captured launch, applied to each launch's algorithmic bytes.
-TRAFFIC = {"tc_fwd_chain": {"bytes_per_sample": (7.346944e6 + 3.011579e9) / 1048576,
-                            "bf16_workload": 2,
-                            "source": "paper_2404_19075_b300/csrc/tc_chain.cu",
-                            "sha256_16": "f3d8542e5a1b0eaf"},
-           "tc_bwd_chain": {"bytes_per_sample": (175.909632e6 + 2.624694e9) / 1048576,
-                            "bf16_workload": 2,
-                            "source": "paper_2404_19075_b300/csrc/tc_chain.cu",
-                            "sha256_16": "f3d8542e5a1b0eaf"},
-           "tc_dw": {"ratio_to_algorithmic": (1.075681e9 + 6.929408e6) / (2 * 1048576 * 512 * 2),
-                     "bf16_workload": 2,
-                     "source": "paper_2404_19075_b300/csrc/tc_gemm.cu",
-                     "sha256_16": "2aa066c32de06e24"}}
+_CHAIN = {"source": "paper_2404_19075_b300/csrc/tc_chain.cu", "sha256_16": "a253b8c374e4fc7d"}
+TRAFFIC = {"tc_fwd_chain": [dict(_CHAIN, bf16_workload=2,
+                                 bytes_per_sample=(7.8912e6 + 3.011638e9) / 1048576),
+                            dict(_CHAIN, bf16_workload=6,
+                                 bytes_per_sample=(54.743e6 + 5.864839e9) / 1048576)],
+           "tc_bwd_chain": [dict(_CHAIN, bf16_workload=2,
+                                 bytes_per_sample=(175.219968e6 + 2.624146e9) / 1048576),
+                            dict(_CHAIN, bf16_workload=6,
+                                 bytes_per_sample=(2.690032e9 + 2.633078e9) / 1048576)],
+           "tc_dw": [{"ratio_to_algorithmic": (1.075681e9 + 6.929408e6) / (2 * 1048576 * 256 * 2),
+                      "bf16_workload": 2,
+                      "source": "paper_2404_19075_b300/csrc/tc_gemm.cu",
+                      "sha256_16": "2aa066c32de06e24"}]}
 
 # Kernels bound by HBM bandwidth (their roofline is GB/s of algorithmic
 # bytes); the others are bound by the tensor pipe.
@@ -73,8 +75,8 @@ def traffic_of(kernel, workload, samples, alg_bytes):
     """DRAM bytes of one launch from the recorded counters, or None when
     there are none for this kernel and workload or its source has changed."""
     import hashlib
-    t = TRAFFIC.get(kernel)
-    if not t or t["bf16_workload"] != workload:
+    t = next((e for e in TRAFFIC.get(kernel, []) if e["bf16_workload"] == workload), None)
+    if t is None:
         return None
     with open(os.path.join(ROOT, t["source"]), "rb") as f:
         if hashlib.sha256(f.read()).hexdigest()[:16] != t["sha256_16"]:
