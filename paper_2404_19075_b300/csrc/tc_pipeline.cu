@@ -166,9 +166,10 @@ __global__ void k_sum_parts(const float *part, int n_parts, long long n, const f
 
 // part[z][c] = sum over rows of split z of w[s] * X[s][c] for BF16 X with C
 // columns (C a multiple of 8). A block of 256 threads reads whole rows as
-// 16-byte vectors (C/8 threads per row, 256/(C/8) rows at a time), keeps
-// eight column sums per thread (blocked summation every 256 rows) and
-// combines the row lanes in shared memory.
+// 16-byte streaming loads (C/8 threads per row, 256/(C/8) rows at a time,
+// eight rows in flight per thread), keeps eight column sums per thread
+// (blocked summation every 256 rows) and combines the row lanes in shared
+// memory.
 __global__ void __launch_bounds__(256)
     k_colsum_bf16(const __nv_bfloat16 *X, int C, long long rows, const float *w, int splits,
                   float *part) {
@@ -183,17 +184,17 @@ __global__ void __launch_bounds__(256)
   if (rl < lanes) {
     int n = 0;
     long long r = r0 + rl;
-    // four rows per step: their loads are in flight together
-    for (; r + 3 * (long long)lanes < r1; r += 4 * (long long)lanes) {
-      uint4 u[4];
-      float wr[4];
+    // eight rows per step: their loads are in flight together
+    for (; r + 7 * (long long)lanes < r1; r += 8 * (long long)lanes) {
+      uint4 u[8];
+      float wr[8];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        u[k] = *reinterpret_cast<const uint4 *>(X + (r + k * lanes) * C + 8 * cv);
+      for (int k = 0; k < 8; ++k) {
+        u[k] = __ldcs(reinterpret_cast<const uint4 *>(X + (r + k * lanes) * C + 8 * cv));
         wr[k] = w[r + k * lanes];
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 8; ++k) {
         const uint32_t v[4] = {u[k].x, u[k].y, u[k].z, u[k].w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(256)
           blk[2 * e + 1] += wr[k] * __uint_as_float(v[e] & 0xFFFF0000u);
         }
       }
-      if ((n += 4) == 256) {
+      if ((n += 8) == 256) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           acc[k] += blk[k];
