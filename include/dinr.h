@@ -248,10 +248,10 @@ DINR_API dinr_status dinr_export(dinr_ctx *ctx, const double *times, int n_times
 /* ----------------------------------------------------------------------
  * Query server (Sec. V: inference from the trained network). Requests of
  * different kinds and sizes are batched continuously: each dinr_serve_step
- * runs one persistent launch over work taken from every in-flight request
- * in arrival order (whole 128-sample tiles, whole rays), so large requests
- * span several launches and requests that arrive in the meantime join the
- * next one. Weights and per-request work lists stay on the device. BF16
+ * runs one persistent launch over work taken from the in-flight requests
+ * in the order of the scheduling policy (whole 128-sample tiles, whole
+ * rays), so large requests span several launches and requests that arrive
+ * in the meantime join the next one. Weights and per-request work lists stay on the device. BF16
  * contexts whose shape runs the fused chain only (DINR_ERR_UNSUPPORTED
  * otherwise).
  * ---------------------------------------------------------------------- */
@@ -276,6 +276,15 @@ typedef struct {
  * 0 keeps the current value (defaults: the workspace; 4 GiB). */
 DINR_API dinr_status dinr_serve_config(dinr_ctx *ctx, int64_t max_batch_samples,
                                        int64_t max_inflight_bytes);
+/* Scheduling policy of the batches. DINR_SERVE_ARRIVAL (the default): work
+ * is taken from requests in arrival order, which keeps the worst latency
+ * lowest when the server is overloaded. DINR_SERVE_LEAST_WORK: from the
+ * requests with the least work left first, so small requests do not queue
+ * behind large ones (lower median latency); a request passed over for 16
+ * batches in a row goes first. Results do not depend on the policy.
+ * DINR_ERR_ARG for an unknown policy. */
+enum { DINR_SERVE_ARRIVAL = 0, DINR_SERVE_LEAST_WORK = 1 };
+DINR_API dinr_status dinr_serve_policy(dinr_ctx *ctx, int policy);
 /* Admit a request. *id receives its handle. DINR_ERR_BUSY: the in-flight
  * budget is full (nothing was admitted; retry after requests complete).
  * The request's input and output memory must stay valid until it is done. */

@@ -58,6 +58,7 @@ class Request(C.Structure):
 
 
 QUERY = {"points": 0, "grid": 1, "project": 2}
+SERVE_POLICY = {"arrival": 0, "least_work": 1}
 
 # dinr_volume_sink(user, k, t, volume, n) -> int
 VOLUME_SINK = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_float),
@@ -92,6 +93,7 @@ PROTOTYPES = {
     "dinr_phantom_project_noalloc": (C.c_int, [C.POINTER(Geometry), C.c_int, vp, vp, vp, vp,
                                                C.c_double, vp, i64, vp, vp]),
     "dinr_serve_config": (C.c_int, [vp, i64, i64]),
+    "dinr_serve_policy": (C.c_int, [vp, C.c_int]),
     "dinr_serve_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_int64)]),
     "dinr_serve_step": (C.c_int, [vp, C.POINTER(C.c_int)]),
     "dinr_serve_poll": (C.c_int, [vp, i64, C.POINTER(C.c_int)]),

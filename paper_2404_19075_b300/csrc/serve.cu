@@ -3,16 +3,20 @@
 // forward-chain launches.
 //
 // Requests are admitted while their outputs fit a budget of in-flight bytes.
-// Every dinr_serve_step builds one batch from all in-flight requests in
-// arrival order (whole 128-sample tiles, whole rays for re-projections), so a
-// large request is spread over several launches and requests that arrive
-// meanwhile join the next one. A batch is one launch of the forward chain
+// Every dinr_serve_step builds one batch from the in-flight requests (whole
+// 128-sample tiles, whole rays for re-projections), so a large request is
+// spread over several launches and requests that arrive meanwhile join the
+// next one. The order is the arrival order, or (least-work policy) the
+// requests with the least work left first, so that a small request is not
+// queued behind a large one; there a request passed over for kMaxSkips
+// batches in a row goes first, so none waits without bound. A batch is one launch of the forward chain
 // over a device work list, followed by the per-item forward model (segment
 // sums of re-projection rays, mu0 * M of voxels). A request is complete when
 // the event recorded after the launch holding its last work has completed.
 #include "context.cuh"
 #include "tc_chain.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <deque>
 #include <vector>
@@ -49,11 +53,14 @@ struct Request {
   long long next = 0;  // next sample to schedule
   long long bytes;     // output bytes (admission)
   cudaEvent_t done_event = nullptr;
-  bool scheduled = false;  // all work launched
+  int skips = 0;           // batches in a row that gave this request no work
 };
+
+constexpr int kMaxSkips = 16;
 
 struct Server {
   long long max_batch = 0, max_inflight = 1LL << 32, inflight = 0;
+  int policy = DINR_SERVE_ARRIVAL;
   long long next_id = 1;
   std::deque<Request> active;          // not yet completely launched
   std::vector<Request> launched;       // completely launched, not yet seen done
@@ -182,6 +189,18 @@ void dinr_serve_release(dinr_ctx *c) {
   c->serve = nullptr;
 }
 
+dinr_status dinr_serve_policy(dinr_ctx *c, int policy) {
+  if (!c) return DINR_ERR_ARG;
+  if (policy != DINR_SERVE_ARRIVAL && policy != DINR_SERVE_LEAST_WORK)
+    return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "unknown serving policy %d", policy);
+  if (!server(c)) {
+    dinr_status s = dinr_serve_config(c, 0, 0);
+    if (s != DINR_OK) return s;
+  }
+  server(c)->policy = policy;
+  return DINR_OK;
+}
+
 dinr_status dinr_serve_submit(dinr_ctx *c, const dinr_request *q, int64_t *id) {
   if (!c || !q || !id) return DINR_ERR_ARG;
   if (c->failed) return DINR_ERR_CUDA;
@@ -220,23 +239,38 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
   if (!sv) return (dinr_status)dinr_fail(c, DINR_ERR_STATE, "no request submitted");
   reap(c, sv);
   if (!sv->active.empty()) {
-    // one batch: whole tiles, whole rays, requests in arrival order
+    // one batch: whole tiles, whole rays; in arrival order, or requests
+    // passed over kMaxSkips times first (in arrival order), then least
+    // remaining work first
+    const size_t na = sv->active.size();
+    std::vector<size_t> ord(na);
+    for (size_t k = 0; k < na; ++k) ord[k] = k;
+    if (sv->policy == DINR_SERVE_LEAST_WORK)
+      std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+        const Request &ra = sv->active[a], &rb = sv->active[b];
+        const bool sa = ra.skips >= kMaxSkips, sb = rb.skips >= kMaxSkips;
+        if (sa != sb) return sa;
+        return !sa && ra.samples - ra.next < rb.samples - rb.next;
+      });
     long long tiles = 0, rec = 0;
     int n_items = 0;
-    std::vector<size_t> finished;
-    std::vector<long long> first_unit(sv->active.size());
+    std::vector<size_t> finished, item_req;
+    std::vector<long long> first_unit(na);
+    std::vector<char> served(na, 0);
     // the staging slot's previous copy must have run before it is rewritten
     const int slot = sv->slot;
     sv->slot = (slot + 1) % Server::kSlots;
     CK(cudaEventSynchronize(sv->slot_event[slot]));
     WorkItem *items_host = sv->items_host + (size_t)slot * sv->max_items;
     int *tile_item_host = sv->tile_item_host + (size_t)slot * sv->max_tiles;
-    for (size_t k = 0; k < sv->active.size() && n_items < sv->max_items; ++k) {
+    for (size_t j = 0; j < na && n_items < sv->max_items; ++j) {
+      const size_t k = ord[j];
       Request &r = sv->active[k];
       long long room = sv->max_batch - tiles * 128;
       long long units = (r.samples - r.next) / r.unit;
       long long fit = room / r.unit;
-      if (fit <= 0) break;
+      if (room <= 0) break;
+      if (fit <= 0) continue;  // a whole ray does not fit; smaller units may
       if (units > fit) units = fit;
       long long n = units * r.unit;
       WorkItem &w = items_host[n_items];
@@ -255,8 +289,11 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
       if (w.kind == kSrcVirtualView) rec += units;
       r.next += n;
       ++n_items;
+      item_req.push_back(k);
+      served[k] = 1;
       if (r.next >= r.samples) finished.push_back(k);
     }
+    for (size_t k = 0; k < na; ++k) sv->active[k].skips = served[k] ? 0 : sv->active[k].skips + 1;
     if (n_items > 0) {
       CK(cudaMemcpyAsync(sv->items_dev, items_host, sizeof(WorkItem) * n_items,
                          cudaMemcpyHostToDevice, c->st));
@@ -274,9 +311,9 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
       dinr_status s = tc_serve_chain(c, sv->items_dev, sv->tile_item_dev, tiles);
       if (s != DINR_OK) return s;
       // forward model of each piece into the request's output
-      size_t k = 0;
-      for (int i = 0; i < n_items; ++i, ++k) {
+      for (int i = 0; i < n_items; ++i) {
         const WorkItem &w = items_host[i];
+        const size_t k = item_req[i];
         Request &r = sv->active[k];
         const float *z = sv->be.zout + w.tile0 * 128;
         if (w.kind == kSrcVirtualView) {
@@ -289,8 +326,9 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
         ++c->launches;
       }
       CK(cudaGetLastError());
-      // completely launched requests leave the active list, newest first; each
-      // owns one event recorded after this batch
+      // completely launched requests leave the active list, highest position
+      // first; each owns one event recorded after this batch
+      std::sort(finished.begin(), finished.end());
       for (size_t f = finished.size(); f-- > 0;) {
         cudaEvent_t ev;
         if (!sv->pool.empty()) {

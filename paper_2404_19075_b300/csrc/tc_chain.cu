@@ -555,7 +555,6 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
     float v[64];
     tmem_ld64(trow + 64 * jc, v);
     uint32_t w[32];
-    uint32_t bits[2] = {0u, 0u};
 #pragma unroll
     for (int i4 = 0; i4 < 16; ++i4) {
       const float4 b = bb[i4];
@@ -563,8 +562,6 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
       const float2 s1 = add2(make_float2(v[4 * i4 + 2], v[4 * i4 + 3]), make_float2(b.z, b.w));
       w[2 * i4] = pack2_relu(s0.x, s0.y);
       w[2 * i4 + 1] = pack2_relu(s1.x, s1.y);
-      bits[i4 >> 3] |= pair_flags(w[2 * i4], (2 * i4) & 15);
-      bits[i4 >> 3] |= pair_flags(w[2 * i4 + 1], (2 * i4 + 1) & 15);
       if (last) {
         const float4 o = ld_keep(p.w_out + 64 * jc + 4 * i4);
         dot = fmaf(fmaxf(s0.x, 0.0f), o.x, dot);
@@ -578,7 +575,12 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
     for (int c16 = 0; c16 < 8; ++c16)
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) =
           make_uint4(w[4 * c16], w[4 * c16 + 1], w[4 * c16 + 2], w[4 * c16 + 3]);
-    if (live && p.masks[L]) st_stream2(mask_unit(p, L, row, jc), make_uint2(bits[0], bits[1]));
+    if (p.masks[L]) {  // bits only for a backward (not for queries)
+      uint32_t bits[2] = {0u, 0u};
+#pragma unroll
+      for (int i = 0; i < 32; ++i) bits[i >> 4] |= pair_flags(w[i], i & 15);
+      if (live) st_stream2(mask_unit(p, L, row, jc), make_uint2(bits[0], bits[1]));
+    }
   }
   fence_async_smem();
   __syncwarp();

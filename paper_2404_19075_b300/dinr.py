@@ -221,6 +221,11 @@ class Dinr:
         self._c(_abi.lib().dinr_serve_config(self._h, int(max_batch_samples),
                                              int(max_inflight_bytes)))
 
+    def serve_policy(self, policy="arrival"):
+        """Batch scheduling of the query server: "arrival" (default) or
+        "least_work" (requests with the least work left first)."""
+        self._c(_abi.lib().dinr_serve_policy(self._h, _abi.SERVE_POLICY[policy]))
+
     def serve_submit(self, kind, out, coords=None, t=0.0, lo=(0, 0, 0), hi=(0, 0, 0),
                      dims=(1, 1, 1), theta=0.0, rows=0, cols=0, S=0):
         """Admit a query writing into the CUDA tensor `out`; returns its id,

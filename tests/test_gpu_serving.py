@@ -69,6 +69,24 @@ def _serve(m, reqs):
     return [o.cpu().numpy() for o in outs]
 
 
+def test_least_work_policy_same_results(model):
+    """The least-work-first schedule reorders the pieces of the batches but
+    not the results: bitwise the arrival-order results."""
+    w, m, theta = model
+    reqs = _requests(seed=3)
+    m.serve_config(max_batch_samples=2048)
+    m.serve_policy("arrival")
+    fifo = _serve(m, reqs)
+    m.serve_policy("least_work")
+    try:
+        lw = _serve(m, reqs)
+    finally:
+        m.serve_policy("arrival")
+    for a, b in zip(fifo, lw):
+        assert np.isfinite(a).all()
+        np.testing.assert_array_equal(a, b)
+
+
 def test_alone_equals_mixed_bitwise(model):
     w, m, theta = model
     reqs = _requests()
