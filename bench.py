@@ -52,15 +52,15 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FM
 # Either bytes per sample of every launch, or (for kernels whose bytes per
 # launch vary by layer) the measured DRAM bytes over the algorithmic bytes of
 # the captured launch, applied to each launch's algorithmic bytes.
-_CHAIN = {"source": "paper_2404_19075_b300/csrc/tc_chain.cu", "sha256_16": "a253b8c374e4fc7d"}
+_CHAIN = {"source": "paper_2404_19075_b300/csrc/tc_chain.cu", "sha256_16": "e51aeb259db074fa"}
 TRAFFIC = {"tc_fwd_chain": [dict(_CHAIN, bf16_workload=2,
-                                 bytes_per_sample=(7.8912e6 + 3.011638e9) / 1048576),
+                                 bytes_per_sample=(7.433728e6 + 3.011451e9) / 1048576),
                             dict(_CHAIN, bf16_workload=6,
-                                 bytes_per_sample=(54.743e6 + 5.864839e9) / 1048576)],
+                                 bytes_per_sample=(56.118e6 + 5.864666e9) / 1048576)],
            "tc_bwd_chain": [dict(_CHAIN, bf16_workload=2,
-                                 bytes_per_sample=(175.219968e6 + 2.624146e9) / 1048576),
+                                 bytes_per_sample=(174.691072e6 + 2.624584e9) / 1048576),
                             dict(_CHAIN, bf16_workload=6,
-                                 bytes_per_sample=(2.690032e9 + 2.633078e9) / 1048576)],
+                                 bytes_per_sample=(2.689914e9 + 2.632930e9) / 1048576)],
            "tc_dw": [{"ratio_to_algorithmic": (1.075681e9 + 6.929408e6) / (2 * 1048576 * 256 * 2),
                       "bf16_workload": 2,
                       "source": "paper_2404_19075_b300/csrc/tc_gemm.cu",
