@@ -253,7 +253,8 @@ def run_reference(args):
             "config": config(w, {"reference_sample_rays_per_step": n_rays}),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": f"{n_rays} rays x {w.geom.samples_per_ray} samples per step"},
+                             "sample": f"{n_rays} rays x {w.geom.samples_per_ray} samples "
+                                       "per step"},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -425,7 +426,8 @@ def run_serving(args, rank):
     sums = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    m.export(ex_times, (-1, -1, -1), (1, 1, 1), ex_dims, lambda k, t, vol: sums.append(float(vol[0, 0, 0])))
+    m.export(ex_times, (-1, -1, -1), (1, 1, 1), ex_dims,
+             lambda k, t, vol: sums.append(float(vol[0, 0, 0])))
     ex_wall = time.perf_counter() - t0
     n_vox = len(ex_times) * ex_dims[0] * ex_dims[1] * ex_dims[2]
     export = {"volumes": len(ex_times), "dims": list(ex_dims), "wall_s": ex_wall,

@@ -263,8 +263,8 @@ static dinr_status f32_loss_grad(dinr_ctx *c, int n) {
     src.idx = c->d_idx + r0;
     {
       ProfScope ps(c, "encode", 0.0, 4.0 * ns * c->ldE);
-      launch_encode_f32(c->geo, src, nr, c->S, c->F, c->grff_c, c->d_grff_B, c->ldE, c->E, c->ray_l, c->d_proj,
-                        c->ray_p, c->st);
+      launch_encode_f32(c->geo, src, nr, c->S, c->F, c->grff_c, c->d_grff_B, c->ldE, c->E,
+                        c->ray_l, c->d_proj, c->ray_p, c->st);
       CKL();
     }
     dinr_status s = f32_hidden(c, ns);
@@ -305,8 +305,8 @@ static dinr_status f32_forward(dinr_ctx *c, const SourceArgs &src0, long long n_
     else
       src.first = src0.first + r0;
     long long ns = nr * S;
-    launch_encode_f32(c->geo, src, nr, S, c->F, c->grff_c, c->d_grff_B, c->ldE, c->E, c->ray_l, nullptr, nullptr,
-                      c->st);
+    launch_encode_f32(c->geo, src, nr, S, c->F, c->grff_c, c->d_grff_B, c->ldE, c->E, c->ray_l,
+                      nullptr, nullptr, c->st);
     CKL();
     dinr_status s = f32_hidden(c, ns);
     if (s != DINR_OK) return s;

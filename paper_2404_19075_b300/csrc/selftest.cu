@@ -36,7 +36,8 @@ dinr_status dinr_selftest_timeout(dinr_ctx *c, int64_t limit_ns) {
     e = cudaGetLastError();
   }
   int code = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&code, flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&code, flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess)
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "selftest: %s", cudaGetErrorString(e));

@@ -9,10 +9,11 @@
 // next one. The order is the arrival order, or (least-work policy) the
 // requests with the least work left first, so that a small request is not
 // queued behind a large one; there a request passed over for kMaxSkips
-// batches in a row goes first, so none waits without bound. A batch is one launch of the forward chain
-// over a device work list, followed by the per-item forward model (segment
-// sums of re-projection rays, mu0 * M of voxels). A request is complete when
-// the event recorded after the launch holding its last work has completed.
+// batches in a row goes first, so none waits without bound. A batch is one
+// launch of the forward chain over a device work list, followed by the
+// per-item forward model (segment sums of re-projection rays, mu0 * M of
+// voxels). A request is complete when the event recorded after the launch
+// holding its last work has completed.
 #include "context.cuh"
 #include "tc_chain.cuh"
 

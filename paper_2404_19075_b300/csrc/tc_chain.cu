@@ -215,7 +215,9 @@ __device__ __forceinline__ int n_pairs(const ChainArgs &p) {
 template <bool kBwd>
 __device__ __forceinline__ int n_steps(const ChainArgs &p) { return kBwd ? p.H - 1 : p.H; }
 template <bool kBwd>
-__device__ __forceinline__ int step_layer(const ChainArgs &p, int i) { return kBwd ? p.H - 1 - i : i; }
+__device__ __forceinline__ int step_layer(const ChainArgs &p, int i) {
+  return kBwd ? p.H - 1 - i : i;
+}
 template <bool kBwd>
 __device__ __forceinline__ int step_k(const ChainArgs &p, int i) {
   return (!kBwd && i == 0) ? p.k0 : p.W;
@@ -700,7 +702,8 @@ __device__ bool bwd_epilogue_swish(const ChainMaps &maps, const ChainArgs &p, co
     if (more) {
 #pragma unroll
       for (int c16 = 0; c16 < 8; ++c16)
-        gn[c16] = live ? ld_stream16(gact_unit(p, L - 1, row, jc + 2, c16)) : make_uint4(0, 0, 0, 0);
+        gn[c16] = live ? ld_stream16(gact_unit(p, L - 1, row, jc + 2, c16))
+                       : make_uint4(0, 0, 0, 0);
     }
     float v[64];
     tmem_ld64(trow + 64 * jc, v);
@@ -799,8 +802,8 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
         const bool last = i == ns - 1;
         const uint32_t tcol = tbase + (uint32_t)(slot * p.W);
         if (kBwd) {
-          if (!bwd_epilogue<kAct>(maps, p, s, slot, tcol, step_layer<true>(p, i), tile, q, half, lane,
-                            waits[slot]++))
+          if (!bwd_epilogue<kAct>(maps, p, s, slot, tcol, step_layer<true>(p, i), tile, q, half,
+                                  lane, waits[slot]++))
             return;
         } else {
           if (!warp_wait(&s.tfull[slot], waits[slot]++ & 1, p.err, 17)) return;

@@ -234,7 +234,8 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
       if (p.epi == kTcFwd) {
         const float4 *b4 = reinterpret_cast<const float4 *>(p.bias + c0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) bb[j] = c0 + 4 * j < p.n_store ? __ldg(b4 + j) : make_float4(0, 0, 0, 0);
+        for (int j = 0; j < 8; ++j)
+          bb[j] = c0 + 4 * j < p.n_store ? __ldg(b4 + j) : make_float4(0, 0, 0, 0);
       }
       float v[32];
       tmem_ld32(trow + ch * 32, v);
@@ -272,9 +273,9 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
           if (p.out8 && c0 + 32 <= p.n_store) {
             uint32_t q8[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) q8[j] = pack_e4m3x4(v[4 * j] * inv_out, v[4 * j + 1] * inv_out,
-                                                        v[4 * j + 2] * inv_out,
-                                                        v[4 * j + 3] * inv_out);
+            for (int j = 0; j < 8; ++j)
+              q8[j] = pack_e4m3x4(v[4 * j] * inv_out, v[4 * j + 1] * inv_out,
+                                  v[4 * j + 2] * inv_out, v[4 * j + 3] * inv_out);
             uint4 *o8 = reinterpret_cast<uint4 *>(p.out8 + (long long)row * p.ldo8 + c0);
             o8[0] = make_uint4(q8[0], q8[1], q8[2], q8[3]);
             o8[1] = make_uint4(q8[4], q8[5], q8[6], q8[7]);
@@ -323,7 +324,8 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
         uint4 *o = reinterpret_cast<uint4 *>(stg + lane * 64);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          o[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]), pack_bf16(v[8 * j + 2], v[8 * j + 3]),
+          o[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]),
+                            pack_bf16(v[8 * j + 2], v[8 * j + 3]),
                             pack_bf16(v[8 * j + 4], v[8 * j + 5]),
                             pack_bf16(v[8 * j + 6], v[8 * j + 7]));
         fence_async_smem();

@@ -714,11 +714,12 @@ dinr_status tc_alloc(dinr_ctx *c) {
   long long pc = (long long)colsum_splits(ns) * c->W;
   t->part_floats = pf > pc ? pf : pc;
   t->chain = chains_used(c);
+  const long long ns_tiles = (ns + 127) / 128 * 128;  // the side streams hold whole tiles
   if (t->chain)
     ok = ok && grab((void **)&t->Dall, 2ull * ns * c->W * c->H) &&
-         (c->act == DINR_ACT_SWISH ? grab((void **)&t->G, 2ull * ((ns + 127) / 128 * 128) * c->W * c->H)
-                                   : grab((void **)&t->masks,
-                                          4ull * ((ns + 127) / 128 * 128) * (c->W / 32) * c->H)) &&
+         (c->act == DINR_ACT_SWISH
+              ? grab((void **)&t->G, 2ull * ns_tiles * c->W * c->H)
+              : grab((void **)&t->masks, 4ull * ns_tiles * (c->W / 32) * c->H)) &&
          grab((void **)&t->rec, 32ull * ns);
   else
     ok = ok && grab((void **)&t->D0, 2ull * ns * c->W) && grab((void **)&t->D1, 2ull * ns * c->W);
@@ -731,7 +732,8 @@ dinr_status tc_alloc(dinr_ctx *c) {
       t->W8.push_back((uint8_t *)w8);
     }
     ok = ok && grab((void **)&t->E8, (size_t)ns * c->ldE) &&
-         grab((void **)&t->H8[0], (size_t)ns * c->W) && grab((void **)&t->H8[1], (size_t)ns * c->W) &&
+         grab((void **)&t->H8[0], (size_t)ns * c->W) &&
+         grab((void **)&t->H8[1], (size_t)ns * c->W) &&
          grab((void **)&t->fscale, 4ull * (1 + 2 * c->H)) &&
          grab((void **)&t->amax_w, 4ull * c->H) && grab((void **)&t->amax_h, 4ull * c->H);
     if (ok) {
@@ -825,8 +827,8 @@ dinr_status tc_loss_grad(dinr_ctx *c, int n) {
     } else {
       {
         ProfScope ps(c, "encode", 0.0, 2.0 * ns * c->ldE);
-        launch_encode_bf16(c->geo, src, nr, c->S, c->F, c->grff_c, c->d_grff_B, c->ldE, t->E, t->ray_l, c->d_proj,
-                           t->ray_p, c->st);
+        launch_encode_bf16(c->geo, src, nr, c->S, c->F, c->grff_c, c->d_grff_B, c->ldE, t->E,
+                           t->ray_l, c->d_proj, t->ray_p, c->st);
         CKL();
       }
       s = forward(c, ns);
@@ -876,8 +878,8 @@ static dinr_status tc_forward(dinr_ctx *c, const SourceArgs &src0, long long n_r
     if (chain_ok(c)) {
       s = chain(c, src, nr, S, false, nullptr);
     } else {
-      launch_encode_bf16(c->geo, src, nr, S, c->F, c->grff_c, c->d_grff_B, c->ldE, t->E, t->ray_l, nullptr, nullptr,
-                         c->st);
+      launch_encode_bf16(c->geo, src, nr, S, c->F, c->grff_c, c->d_grff_B, c->ldE, t->E,
+                         t->ray_l, nullptr, nullptr, c->st);
       CKL();
       s = forward(c, ns);
     }
