@@ -200,6 +200,16 @@ __device__ __forceinline__ uint32_t pair_mask(uint32_t m, int k) {
   asm("prmt.b32 %0, %1, %1, 0xBB99;" : "=r"(d) : "r"(m << k));
   return d;
 }
+// The same from ms = m << (k % 8): pairs k and k + 8 share the shift, their
+// bits landing at the top of bytes 1 and 3 (k < 8) or bytes 0 and 2.
+__device__ __forceinline__ uint32_t pair_mask_sh(uint32_t ms, int k) {
+  uint32_t d;
+  if (k < 8)
+    asm("prmt.b32 %0, %1, %1, 0xBB99;" : "=r"(d) : "r"(ms));
+  else
+    asm("prmt.b32 %0, %1, %1, 0xAA88;" : "=r"(d) : "r"(ms));
+  return d;
+}
 
 // Tiles of this CTA: blockIdx.x + k * gridDim.x, processed in pairs.
 __device__ __forceinline__ long long tile_of(const ChainArgs &p, int pair, int slot) {
@@ -753,15 +763,22 @@ __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Sm
     float v[64];
     tmem_ld64(trow + 64 * jc, v);
     const uint2 m2 = k == 0 ? mb[0] : mb[1];
+    uint32_t msx[8], msy[8];  // the mask words shifted by 0..7
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      msx[j] = m2.x << j;
+      msy[j] = m2.y << j;
+    }
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
 #pragma unroll
     for (int c16 = 0; c16 < 8; ++c16) {
-      const uint32_t m = c16 < 4 ? m2.x : m2.y;
       uint32_t w[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int i = 8 * c16 + 2 * e;
-        w[e] = pack2(v[i], v[i + 1]) & pair_mask(m, (4 * c16 + e) & 15);
+        const int pk = (4 * c16 + e) & 15;
+        const uint32_t ms = c16 < 4 ? msx[pk & 7] : msy[pk & 7];
+        w[e] = pack2(v[i], v[i + 1]) & pair_mask_sh(ms, pk);
       }
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
