@@ -52,15 +52,15 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FM
 # Either bytes per sample of every launch, or (for kernels whose bytes per
 # launch vary by layer) the measured DRAM bytes over the algorithmic bytes of
 # the captured launch, applied to each launch's algorithmic bytes.
-_CHAIN = {"source": "paper_2404_19075_b300/csrc/tc_chain.cu", "sha256_16": "e445eb74ed98cfb6"}
+_CHAIN = {"source": "paper_2404_19075_b300/csrc/tc_chain.cu", "sha256_16": "aedccfdd470b96ae"}
 TRAFFIC = {"tc_fwd_chain": [dict(_CHAIN, bf16_workload=2,
-                                 bytes_per_sample=(6.9568e6 + 3.011905e9) / 1048576),
+                                 bytes_per_sample=(8.475648e6 + 3.011426e9) / 1048576),
                             dict(_CHAIN, bf16_workload=6,
-                                 bytes_per_sample=(53.299e6 + 5.865255e9) / 1048576)],
+                                 bytes_per_sample=(55.972e6 + 5.865002e9) / 1048576)],
            "tc_bwd_chain": [dict(_CHAIN, bf16_workload=2,
-                                 bytes_per_sample=(176.854784e6 + 2.624417e9) / 1048576),
+                                 bytes_per_sample=(174.985216e6 + 2.629659e9) / 1048576),
                             dict(_CHAIN, bf16_workload=6,
-                                 bytes_per_sample=(2.689983e9 + 2.632958e9) / 1048576)],
+                                 bytes_per_sample=(2.690049e9 + 2.632700e9) / 1048576)],
            "tc_dw": [{"ratio_to_algorithmic": (1.075681e9 + 6.929408e6) / (2 * 1048576 * 256 * 2),
                       "bf16_workload": 2,
                       "source": "paper_2404_19075_b300/csrc/tc_gemm.cu",
