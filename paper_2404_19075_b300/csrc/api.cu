@@ -2,6 +2,8 @@
 // and dispatch to the step / query pipelines.
 #include "context.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -642,6 +644,7 @@ static cudaEvent_t prof_event(dinr_ctx *c) {
 }
 
 ProfScope::ProfScope(dinr_ctx *ctx, const char *name, double flops, double bytes) : c(ctx) {
+  nvtxRangePushA(name);
   if (!c || !c->prof) return;
   int cls = -1;
   for (size_t i = 0; i < c->prof_names.size(); ++i)
@@ -659,6 +662,7 @@ ProfScope::ProfScope(dinr_ctx *ctx, const char *name, double flops, double bytes
 
 ProfScope::~ProfScope() {
   if (idx >= 0) cudaEventRecord(c->prof_recs[idx].b, c->st);
+  nvtxRangePop();
 }
 
 dinr_status dinr_profile(dinr_ctx *c, int enable) {

@@ -76,7 +76,8 @@ int dinr_fail(dinr_ctx *c, int status, const char *fmt, ...);
 void dinr_serve_release(dinr_ctx *c);
 
 // Brackets the launches issued in its scope with two events on the context
-// stream when profiling is on.
+// stream when profiling is on, and always with an NVTX range of the same
+// name (free without a tool attached; ncu --nvtx and nsys pick them up).
 struct ProfScope {
   dinr_ctx *c;
   int idx = -1;
