@@ -52,7 +52,9 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FM
 # Either bytes per sample of every launch, or (for kernels whose bytes per
 # launch vary by layer) the measured DRAM bytes over the algorithmic bytes of
 # the captured launch, applied to each launch's algorithmic bytes.
-_CHAIN = {"source": "paper_2404_19075_b300/csrc/tc_chain.cu", "sha256_16": "aedccfdd470b96ae"}
+_CSRC = "paper_2404_19075_b300/csrc/"
+_CHAIN = {"source": [_CSRC + f for f in ("tc_chain.cu", "tc_chain.cuh", "tc_ptx.cuh")],
+          "sha256_16": "ad0a35d0af6fd433"}
 TRAFFIC = {"tc_fwd_chain": [dict(_CHAIN, bf16_workload=2,
                                  bytes_per_sample=(8.475648e6 + 3.011426e9) / 1048576),
                             dict(_CHAIN, bf16_workload=6,
@@ -61,26 +63,34 @@ TRAFFIC = {"tc_fwd_chain": [dict(_CHAIN, bf16_workload=2,
                                  bytes_per_sample=(174.985216e6 + 2.629659e9) / 1048576),
                             dict(_CHAIN, bf16_workload=6,
                                  bytes_per_sample=(2.690049e9 + 2.632700e9) / 1048576)],
-           "tc_dw": [{"ratio_to_algorithmic": (1.075681e9 + 6.929408e6) / (2 * 1048576 * 256 * 2),
+           "tc_dw": [{"ratio_to_algorithmic": (1.075507e9 + 6.65728e6) / (2 * 1048576 * 256 * 2),
                       "bf16_workload": 2,
-                      "source": "paper_2404_19075_b300/csrc/tc_gemm.cu",
-                      "sha256_16": "2aa066c32de06e24"}]}
+                      "source": [_CSRC + f for f in ("tc_gemm.cu", "tc_gemm.cuh", "tc_ptx.cuh")],
+                      "sha256_16": "de117760effc7867"}]}
 
 # Kernels bound by HBM bandwidth (their roofline is GB/s of algorithmic
 # bytes); the others are bound by the tensor pipe.
 HBM_BOUND = {"tc_dw", "dw_out", "encode"}
 
 
+def source_hash(paths):
+    """First 16 hex digits of the SHA-256 of the files' bytes, concatenated."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_of(kernel, workload, samples, alg_bytes):
     """DRAM bytes of one launch from the recorded counters, or None when
     there are none for this kernel and workload or its source has changed."""
-    import hashlib
     t = next((e for e in TRAFFIC.get(kernel, []) if e["bf16_workload"] == workload), None)
     if t is None:
         return None
-    with open(os.path.join(ROOT, t["source"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest()[:16] != t["sha256_16"]:
-            return None
+    if source_hash(t["source"]) != t["sha256_16"]:
+        return None
     if "bytes_per_sample" in t:
         return t["bytes_per_sample"] * samples
     return t["ratio_to_algorithmic"] * alg_bytes
