@@ -234,6 +234,22 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Blocks of the output-layer column sum: at most one full wave (SMs x the
+// blocks an SM holds), so that no partial second wave trails the sum, and
+// no more than colsum_splits (the size of the partials buffer).
+int colsum_bf16_splits(int num_sms, long long rows) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colsum_bf16, 256, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  const long long wave = (long long)num_sms * per_sm;
+  const long long cap = colsum_splits(rows);
+  return (int)(cap < wave ? cap : wave);
+}
+
 int splits_for(long long rows, int m_tiles, int num_sms) {
   long long s = num_sms / m_tiles;
   long long by_rows = (rows + 4095) / 4096;  // at least 4096 samples per split
@@ -557,7 +573,7 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
         t->D0);
     CKL();
   }
-  int cs = colsum_splits(ns);
+  int cs = colsum_bf16_splits(t->num_sms, ns);
   dinr_status s;
   {
     ProfScope ps(c, "dw_out", 2.0 * ns * W, 2.0 * ns * W + 4.0 * ns);
