@@ -452,18 +452,31 @@ void launch_colsum(const float *X, long long ld, int C, long long rows, const fl
   k_colsum<<<grid, 256, 0, st>>>(X, ld, C, rows, w, apply_act ? 1 : 0, act, splits, part);
 }
 
-__global__ void k_reduce_partials(const float *part, int splits, long long C, float *out,
-                                  int accumulate) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  float acc = accumulate ? out[c] : 0.0f;
+// out[c] (+)= sum over z of part[z][c] in a fixed order: a block takes 32
+// consecutive elements; each of its 8 warps sums the splits z = g, g + 8, ...
+// of them (coalesced 128-byte rows, 8 times the loads in flight of one
+// thread per element), and one thread per element adds the 8 warp sums in
+// order.
+__global__ void __launch_bounds__(256)
+    k_reduce_partials(const float *part, int splits, long long C, float *out, int accumulate) {
+  __shared__ float red[8][33];
+  const int e = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const long long c = blockIdx.x * 32LL + e;
   float s = 0.0f;
-  for (int z = 0; z < splits; ++z) s += part[(long long)z * C + c];
-  out[c] = acc + s;
+  if (c < C)
+    for (int z = g; z < splits; z += 8) s += part[(long long)z * C + c];
+  red[g][e] = s;
+  __syncthreads();
+  if (g == 0 && c < C) {
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += red[k][e];
+    out[c] = (accumulate ? out[c] : 0.0f) + t;
+  }
 }
 void launch_reduce_partials(const float *part, int splits, long long C, float *out,
                             bool accumulate, cudaStream_t st) {
-  k_reduce_partials<<<ceil_div(C, 256), 256, 0, st>>>(part, splits, C, out, accumulate ? 1 : 0);
+  k_reduce_partials<<<ceil_div(C, 32), 256, 0, st>>>(part, splits, C, out, accumulate ? 1 : 0);
 }
 
 // One block, fixed order: strided partial sums then a tree.
