@@ -87,6 +87,44 @@ def test_least_work_policy_same_results(model):
         np.testing.assert_array_equal(a, b)
 
 
+def test_least_work_policy_does_not_starve(model):
+    """Under the least-work policy a large request keeps making progress
+    while small ones fill every batch: after 16 batches without work it goes
+    first, so it completes (and bitwise equals the single query)."""
+    w, m, theta = model
+    m.serve_config(max_batch_samples=2048)
+    m.serve_policy("least_work")
+    try:
+        kw = dict(t=0.4, lo=(-1, -1, -1), hi=(1, 1, 1), dims=(40, 40, 40))
+        big = torch.full((40 ** 3,), float("nan"), device="cuda")
+        rid = m.serve_submit("grid", big, **kw)
+        assert rid is not None
+        small = []
+        done = False
+        for step in range(3000):
+            for _ in range(2):  # two 1,024-sample requests fill a 2,048-sample batch
+                o = torch.empty(1024, device="cuda")
+                assert m.serve_submit("grid", o, t=0.6, lo=(-0.5, -0.5, -0.5),
+                                      hi=(0.5, 0.5, 0.5), dims=(16, 16, 4)) is not None
+                small.append(o)
+            m.serve_step()
+            if m.serve_poll(rid):
+                done = True
+                break
+        assert done, "the large request starved"
+        # 32 batches of its own work, at least one in every 17, plus the few
+        # batches the host runs ahead of the GPU
+        assert step < 800
+        for _ in range(100000):  # let the small requests drain
+            if m.serve_step() == 0:
+                break
+    finally:
+        m.serve_policy("arrival")
+    torch.cuda.synchronize()
+    single = m.query_grid(kw["t"], kw["lo"], kw["hi"], kw["dims"]).cpu().numpy().ravel()
+    assert np.array_equal(big.cpu().numpy(), single)
+
+
 def test_alone_equals_mixed_bitwise(model):
     w, m, theta = model
     reqs = _requests()
