@@ -12,29 +12,10 @@ import pytest
 from oracle import step as ostep
 from synthetic import workloads as wl
 
-from gpu_util import assert_close, make_model, require_gpu, split_grad
+from gpu_util import assert_close, check_step, make_model, require_gpu
 
 pytestmark = pytest.mark.gpu
 TOL = {"fp32": 1e-5, "bf16": 2e-2}
-
-
-def _check(m, w, net, theta, idx, proj, prec, decide=None):
-    """p_bar, loss and every layer's weight and bias gradients within the
-    path's tolerance. The output layer's bias gradient is one number, a sum
-    of signed residuals p_bar - p over the batch in which cancellation
-    magnifies the rounding of p_bar; it is checked together with the output
-    weights' gradient as one tensor (norm-wise and element-wise)."""
-    ref = ostep.loss_and_grad(theta, w.geom, net, idx, proj.astype(np.float64), decide=decide)
-    assert_close(m.predict(idx).cpu().numpy(), ref["p_bar"], TOL[prec], "p_bar")
-    loss, grad = m.loss_grad(idx)
-    assert abs(loss.item() - ref["loss"]) <= TOL[prec] * ref["loss"]
-    g = grad.cpu().numpy()
-    pairs = list(zip(split_grad(g, net), split_grad(ref["grad"], net)))
-    for L, ((gw, gb), (ow, ob)) in enumerate(pairs[:-1]):
-        assert_close(gw, ow, TOL[prec], f"dW layer {L}")
-        assert_close(gb, ob, TOL[prec], f"db layer {L}")
-    (gw, gb), (ow, ob) = pairs[-1]
-    assert_close(np.concatenate([gw, gb]), np.concatenate([ow, ob]), TOL[prec], "output layer")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -43,7 +24,7 @@ def test_paper_network_parity_size(prec):
     w = wl.workload(7)
     idx = wl.ray_subset(w.geom.n_proj, 1024, w.seeds["sampler"])
     m, theta, proj = make_model(w, prec, idx=idx)
-    _check(m, w, w.net, theta, idx, proj, prec)
+    check_step(m, w, w.net, theta, idx, proj, prec)
     m.close()
 
 
@@ -55,7 +36,7 @@ def test_grff_relu_fused_chain():
     m, theta, proj = make_model(w, "bf16", idx=idx, net=net,
                                 params=wl.he_init(net, w.seeds["weights"]))
     m.profile(True)
-    _check(m, w, net, theta, idx, proj, "bf16", decide="bf16")
+    check_step(m, w, net, theta, idx, proj, "bf16", decide="bf16")
     m.profile(False)
     assert "tc_fwd_chain" in m.profile_report()
     pts = np.random.default_rng(3).uniform(-0.9, 0.9, (300, 4))
@@ -72,7 +53,7 @@ def test_paper_network_full_size_subset(prec, n):
     w = wl.workload(6)
     idx = wl.ray_subset(w.geom.n_proj, n, 606)
     m, theta, proj = make_model(w, prec, idx=idx, batch=256)
-    _check(m, w, w.net, theta, idx, proj, prec)
+    check_step(m, w, w.net, theta, idx, proj, prec)
     m.close()
 
 
@@ -87,7 +68,7 @@ def test_swish_fused_chains_and_serving():
     m, theta, proj = make_model(w, "bf16", idx=idx, net=net,
                                 params=wl.he_init(net, w.seeds["weights"]))
     m.profile(True)
-    _check(m, w, net, theta, idx, proj, "bf16")
+    check_step(m, w, net, theta, idx, proj, "bf16")
     m.profile(False)
     rep = m.profile_report()
     assert "tc_fwd_chain" in rep and "tc_bwd_chain" in rep
