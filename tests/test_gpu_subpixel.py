@@ -85,3 +85,28 @@ def test_subpixel_paper_network_full_size_subset(prec, n):
     m, theta, proj = make_model(w, prec, idx=idx, batch=64)
     _check(m, w, w.geom, w.net, theta, idx, proj, prec)
     m.close()
+
+
+@pytest.mark.parametrize("prec,act,C,F", [("fp32", "swish", 32, 0), ("bf16", "swish", 32, 0),
+                                          ("bf16", "relu", 0, 6)])
+def test_subpixel_cone_beam(prec, act, C, F):
+    """App. A on a cone-beam geometry (source-to-object 4, source-to-
+    detector 8): sub-rays from the source to the sub-pixel centres, spacing
+    scaled to the rotation axis; the paper's network (FP32 path, BF16
+    unfused) and an octave ReLU network through the fused chains."""
+    require_gpu()
+    w9 = wl.workload(9)
+    k = np.arange(64.0)
+    geom = replace(wl.cone_geometry(64, 32, 32, 2 * np.pi * k / 64, k / 64, 32), subpixels=2)
+    w = replace(w9, geom=geom)
+    enc = "grff" if C else "octave"
+    net = replace(w9.net, act=act, encoding=enc, grff_c=C, n_freq=F,
+                  width=128 if act == "relu" else w9.net.width)
+    idx = wl.ray_subset(geom.n_proj, 256, 17)
+    m, theta, proj = make_model(w, prec, idx=idx, net=net, batch=256,
+                                params=wl.he_init(net, w.seeds["weights"]))
+    try:
+        _check(m, w, geom, net, theta, idx, proj, prec,
+               decide="bf16" if act == "relu" else None)
+    finally:
+        m.close()

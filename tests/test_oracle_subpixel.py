@@ -82,3 +82,40 @@ def test_subpixel_loss_central_differences():
     for k in ks:
         fd = step.fd_grad(theta, g, net, idx, proj, k, h=1e-5)
         assert abs(fd - out["grad"][k]) <= 1e-7 * max(1e-3, np.abs(out["grad"]).max()), k
+
+
+def test_cone_subrays_by_brute_force():
+    """Cone beam, view 0 (theta = 0): each sub-ray starts at the source
+    (0, -SOD, 0) and points at its sub-pixel centre (u, SDD - SOD, v); its
+    chord length matches a brute-force count of points inside the FOV
+    (x^2 + y^2 <= 1, |z| <= 1) along the line, and its sample count is the
+    fewest equal parts no longer than the spacing, the pixel pitch scaled to
+    the rotation axis (SOD / SDD) over D."""
+    k = np.arange(16.0)
+    g = replace(wl.cone_geometry(16, 32, 32, 2 * np.pi * k / 16, k / 16, 32), subpixels=2)
+    D = g.subpixels
+    rows, cols = np.array([2, 15, 16, 29, 0]), np.array([4, 15, 17, 27, 31])
+    idx = rows * g.det_cols + cols                      # view 0
+    o, d, s0, l, t = geometry.subpixel_rays(g, idx)
+    kk = np.arange(len(idx) * D * D)
+    pix, a, b = kk // (D * D), (kk % (D * D)) // D, kk % D
+    u = g.det_off_u + (cols[pix] + (b + 0.5) / D) * g.det_pitch_u
+    v = g.det_off_v + (rows[pix] + (a + 0.5) / D) * g.det_pitch_v
+    target = np.stack([u, np.full_like(u, g.sdd - g.sod), v], 1)
+    assert np.allclose(o, [0.0, -g.sod, 0.0], atol=1e-14)
+    want_d = target - o
+    want_d /= np.linalg.norm(want_d, axis=1, keepdims=True)
+    assert np.allclose(d, want_d, atol=1e-14)
+    h = 2e-5
+    s = np.arange(0.0, g.sod + 2.0, h) + h / 2
+    for r in range(len(l)):
+        P = o[r] + s[:, None] * d[r]
+        inside = (P[:, 0] ** 2 + P[:, 1] ** 2 <= 1.0) & (np.abs(P[:, 2]) <= 1.0)
+        assert abs(inside.sum() * h - l[r]) <= 2 * h
+    delta = min(g.det_pitch_u, g.det_pitch_v) * g.sod / g.sdd / D
+    assert abs(geometry.sample_spacing(g) - delta) <= 1e-15
+    n = geometry.subpixel_counts(g, l)
+    full = l > 0
+    assert (l[full] / n[full] <= delta * (1 + 1e-12)).all()
+    assert (l[full] / np.maximum(n[full] - 1, 1e-300) > delta).all()
+    assert (n[~full] == 0).all()
