@@ -251,9 +251,11 @@ DINR_API dinr_status dinr_export(dinr_ctx *ctx, const double *times, int n_times
  * runs one persistent launch over work taken from the in-flight requests
  * in the order of the scheduling policy (whole 128-sample tiles, whole
  * rays), so large requests span several launches and requests that arrive
- * in the meantime join the next one. Weights and per-request work lists stay on the device. BF16
- * contexts whose shape runs the fused chain only (DINR_ERR_UNSUPPORTED
- * otherwise).
+ * in the meantime join the next one. Weights and per-request work lists
+ * stay on the device. Contexts whose network the fused chain does not take
+ * (FP32, FP8, BF16 widths above 256) are served with the same admission and
+ * scheduling, the pieces of a batch running one after another through the
+ * single-query path (bitwise the results of the single-query calls).
  * ---------------------------------------------------------------------- */
 enum { DINR_QUERY_POINTS = 0, DINR_QUERY_GRID = 1, DINR_QUERY_PROJECT = 2 };
 typedef struct {

@@ -12,8 +12,11 @@
 // batches in a row goes first, so none waits without bound. A batch is one
 // launch of the forward chain over a device work list, followed by the
 // per-item forward model (segment sums of re-projection rays, mu0 * M of
-// voxels). A request is complete when the event recorded after the launch
-// holding its last work has completed.
+// voxels). Networks the fused chain does not take (FP32 contexts, BF16
+// widths above 256) run the pieces of a batch one after another through the
+// single-query path instead, with the same scheduling. A request is complete
+// when the event recorded after the launch holding its last work has
+// completed.
 #include "context.cuh"
 #include "tc_chain.cuh"
 
@@ -62,6 +65,7 @@ constexpr int kMaxSkips = 16;
 struct Server {
   long long max_batch = 0, max_inflight = 1LL << 32, inflight = 0;
   int policy = DINR_SERVE_ARRIVAL;
+  bool chain = true;  // one fused-chain launch per batch, else piece by piece
   long long next_id = 1;
   std::deque<Request> active;          // not yet completely launched
   std::vector<Request> launched;       // completely launched, not yet seen done
@@ -140,11 +144,11 @@ dinr_status dinr_serve_config(dinr_ctx *c, int64_t max_batch_samples, int64_t ma
   Server *sv = server(c);
   if (!sv) {
     ServeBackend be{};
-    if (!tc_serve_backend(c, &be))
-      return (dinr_status)dinr_fail(c, DINR_ERR_UNSUPPORTED,
-                                    "serving needs the BF16 fused-chain path");
+    const bool chain = tc_serve_backend(c, &be);
+    if (!chain) be.capacity = (long long)c->chunk_rays * c->S;  // the single-query passes
     sv = new Server();
     sv->be = be;
+    sv->chain = chain;
     sv->max_items = 4096;
     sv->max_tiles = be.capacity / 128 + sv->max_items;
     void *p = nullptr;
@@ -296,37 +300,51 @@ dinr_status dinr_serve_step(dinr_ctx *c, int *in_flight) {
     }
     for (size_t k = 0; k < na; ++k) sv->active[k].skips = served[k] ? 0 : sv->active[k].skips + 1;
     if (n_items > 0) {
-      CK(cudaMemcpyAsync(sv->items_dev, items_host, sizeof(WorkItem) * n_items,
-                         cudaMemcpyHostToDevice, c->st));
-      CK(cudaMemcpyAsync(sv->tile_item_dev, tile_item_host, sizeof(int) * tiles,
-                         cudaMemcpyHostToDevice, c->st));
-      CK(cudaEventRecord(sv->slot_event[slot], c->st));
-      // ray records of the re-projection pieces
-      for (int i = 0; i < n_items; ++i) {
-        const WorkItem &w = items_host[i];
-        if (w.kind != kSrcVirtualView) continue;
-        launch_ray_records(c->geo, w.src, w.n / w.S, w.S, sv->be.rec + 8 * w.rec0,
-                           sv->be.ray_l + w.rec0, nullptr, nullptr, c->st);
-        ++c->launches;
-      }
-      dinr_status s = tc_serve_chain(c, sv->items_dev, sv->tile_item_dev, tiles);
-      if (s != DINR_OK) return s;
-      // forward model of each piece into the request's output
-      for (int i = 0; i < n_items; ++i) {
-        const WorkItem &w = items_host[i];
-        const size_t k = item_req[i];
-        Request &r = sv->active[k];
-        const float *z = sv->be.zout + w.tile0 * 128;
-        if (w.kind == kSrcVirtualView) {
-          launch_segsum(z, c->out_act, w.n / w.S, w.S, c->mu0, sv->be.ray_l + w.rec0, nullptr,
-                        1.0f, false, r.q.out_dev + first_unit[k], nullptr, nullptr, c->st);
-        } else {
-          launch_segsum(z, c->out_act, w.n, 1, c->mu0, sv->be.ones, nullptr, 1.0f, false,
-                        r.q.out_dev + first_unit[k], nullptr, nullptr, c->st);
+      if (!sv->chain) {
+        // piece by piece through the single-query path (bitwise the same
+        // results as the single queries)
+        for (int i = 0; i < n_items; ++i) {
+          const WorkItem &w = items_host[i];
+          const size_t k = item_req[i];
+          float *out = sv->active[k].q.out_dev + first_unit[k];
+          dinr_status s = w.kind == kSrcVirtualView
+                              ? run_forward_rays(c, w.src, w.n / w.S, w.S, out)
+                              : run_forward_points(c, w.src, w.n, out);
+          if (s != DINR_OK) return s;
         }
-        ++c->launches;
+      } else {
+        CK(cudaMemcpyAsync(sv->items_dev, items_host, sizeof(WorkItem) * n_items,
+                           cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(sv->tile_item_dev, tile_item_host, sizeof(int) * tiles,
+                           cudaMemcpyHostToDevice, c->st));
+        CK(cudaEventRecord(sv->slot_event[slot], c->st));
+        // ray records of the re-projection pieces
+        for (int i = 0; i < n_items; ++i) {
+          const WorkItem &w = items_host[i];
+          if (w.kind != kSrcVirtualView) continue;
+          launch_ray_records(c->geo, w.src, w.n / w.S, w.S, sv->be.rec + 8 * w.rec0,
+                             sv->be.ray_l + w.rec0, nullptr, nullptr, c->st);
+          ++c->launches;
+        }
+        dinr_status s = tc_serve_chain(c, sv->items_dev, sv->tile_item_dev, tiles);
+        if (s != DINR_OK) return s;
+        // forward model of each piece into the request's output
+        for (int i = 0; i < n_items; ++i) {
+          const WorkItem &w = items_host[i];
+          const size_t k = item_req[i];
+          Request &r = sv->active[k];
+          const float *z = sv->be.zout + w.tile0 * 128;
+          if (w.kind == kSrcVirtualView) {
+            launch_segsum(z, c->out_act, w.n / w.S, w.S, c->mu0, sv->be.ray_l + w.rec0, nullptr,
+                          1.0f, false, r.q.out_dev + first_unit[k], nullptr, nullptr, c->st);
+          } else {
+            launch_segsum(z, c->out_act, w.n, 1, c->mu0, sv->be.ones, nullptr, 1.0f, false,
+                          r.q.out_dev + first_unit[k], nullptr, nullptr, c->st);
+          }
+          ++c->launches;
+        }
+        CK(cudaGetLastError());
       }
-      CK(cudaGetLastError());
       // completely launched requests leave the active list, highest position
       // first; each owns one event recorded after this batch
       std::sort(finished.begin(), finished.end());
