@@ -90,7 +90,8 @@ enum { DINR_ENC_OCTAVE = 0, DINR_ENC_GRFF = 1 };
  *         forward-only calls use the current scales and do not update
  *         them) and FP32 accumulation; the backward is the BF16 one, run on
  *         the BF16 copies of the same activations. Unfused GEMMs only (no
- *         fused chains, no recomputation, no query server). */
+ *         fused chains, no recomputation; the query server runs its
+ *         requests through the single-query path). */
 enum { DINR_PREC_FP32 = 0, DINR_PREC_BF16 = 1, DINR_PREC_FP8 = 2 };
 
 typedef struct dinr_ctx dinr_ctx;

@@ -1,5 +1,6 @@
 """The query server on networks the fused chain does not take: an FP32
-context and a BF16 context of width 512 (two 256-column N tiles).
+context, a BF16 context of width 512 (two 256-column N tiles) and an FP8
+context.
 The same mixed requests as the fused-chain tests, in small batches so that
 large requests span several pieces: every result bitwise equals the
 single-query call of the same request."""
@@ -24,7 +25,7 @@ def _single(m, kind, kw):
     return m.project(kw["theta"], kw["t"], kw["rows"], kw["cols"], kw["S"]).cpu().numpy().ravel()
 
 
-@pytest.mark.parametrize("prec,W", [("fp32", 64), ("bf16", 512)])
+@pytest.mark.parametrize("prec,W", [("fp32", 64), ("bf16", 512), ("fp8", 256)])
 def test_served_equals_single_queries(prec, W):
     require_gpu()
     w = wl.workload(1)
