@@ -70,7 +70,7 @@ typedef enum {
   DINR_ERR_CUDA = 3,         /* a CUDA call failed; the context is now unusable */
   DINR_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
   DINR_ERR_NONFINITE = 5,    /* the loss of a step was NaN or infinite */
-  DINR_ERR_UNSUPPORTED = 6,  /* the shape or mode is not supported by this build */
+  DINR_ERR_UNSUPPORTED = 6,  /* the shape or mode is not supported by the library */
   DINR_ERR_BUSY = 7,         /* the request cannot be admitted now */
   DINR_ERR_STATE = 8         /* the call is out of order or the state blob is bad */
 } dinr_status;
