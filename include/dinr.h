@@ -348,17 +348,22 @@ DINR_API dinr_status dinr_phantom_project(const dinr_geometry *geom, int n_ell,
  * other allocating routine. The paper has no counterpart: it is a property
  * of this library, not of the method.
  *   Limits: n_views <= 4096 and n_ell <= 1024, otherwise DINR_ERR_ARG. The
- *   array (320 KiB) lives on every GPU that loads the library until the
+ *   array (208 KiB) lives on every GPU that loads the library until the
  *   process exits.
- *   The first call on a device looks the array's device address up (once
- *   per device, with that device current); make that first call before any
- *   stream capture.
+ *   The first call on a device looks the array's device address up (with
+ *   that device current) and caches it for the device's context; make that
+ *   first call before any stream capture. If the device's context changes
+ *   (after cudaDeviceReset, say), the next call looks the address up again.
  *   All calls on a device share the array, which keeps the last call's
  *   contents: calls whose work overlaps on the GPU (for example on two
  *   streams at once) race and give wrong results; serialise them.
- *   Arguments, output and errors as dinr_phantom_project, except that the
- *   call does not wait for the stream: out_dev is ready when the stream
- *   reaches the end of the call's work. */
+ *   The host arrays (geometry tables, centre, axes, rho, vel) are read only
+ *   during the call: the view table and ellipsoid records are built from
+ *   them in a static host buffer and copied from there, so the caller may
+ *   change or free them once the call returns.
+ *   Arguments, output and errors as dinr_phantom_project (the same geometry
+ *   checks), except that the call does not wait for the stream: out_dev is
+ *   ready when the stream reaches the end of the call's work. */
 DINR_API dinr_status dinr_phantom_project_noalloc(const dinr_geometry *geom, int n_ell,
                                                   const double *centre, const double *axes,
                                                   const double *rho, const double *vel,

@@ -103,18 +103,6 @@ static void *dev_alloc(dinr_ctx *c, size_t bytes, bool *ok) {
   return p;
 }
 
-static int check_geometry(const dinr_geometry *g) {
-  if (!g || !g->view_angle || !g->view_time) return 0;
-  if (g->beam != DINR_BEAM_PARALLEL && g->beam != DINR_BEAM_CONE) return 0;
-  if (g->n_views < 1 || g->det_rows < 1 || g->det_cols < 1) return 0;
-  if (!(g->det_pitch_u > 0) || !(g->det_pitch_v > 0) || !(g->fov_r > 0)) return 0;
-  if (!(g->fov_z1 > g->fov_z0) || !(g->t1 > g->t0)) return 0;
-  if (g->samples_per_ray < 1 || g->samples_per_ray > 4096) return 0;
-  if (g->beam == DINR_BEAM_CONE && (!(g->sod > g->fov_r) || !(g->sdd > g->sod))) return 0;
-  if (g->subpixels < 0 || g->subpixels > 8) return 0;
-  return 1;
-}
-
 // Device geometry tables from the host description (FP64, per view).
 static dinr_status setup_geometry(dinr_ctx *c, const dinr_geometry *g, GeoDev *geo,
                                   double2 **cs_out, double **tbar_out, double **t_out,
@@ -184,7 +172,7 @@ dinr_status dinr_create(const dinr_geometry *geom, const dinr_net *net, const di
                         dinr_ctx **out) {
   if (!out) return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (!check_geometry(geom))
+  if (!dinr_geometry_valid(geom))
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid geometry");
   if (!net || net->n_freq < 0 || net->n_freq > kMaxFreq || net->hidden_layers < 1 ||
       net->hidden_layers > 32 || net->width < 1 || net->width > 1024 ||
@@ -595,7 +583,7 @@ dinr_status dinr_phantom_project(const dinr_geometry *geom, int n_ell, const dou
                                  const double *axes, const double *rho, const double *vel,
                                  double growth, const int64_t *idx, int64_t n, float *out,
                                  void *cuda_stream) {
-  if (!check_geometry(geom) || n_ell < 0 || (n_ell > 0 && (!centre || !axes || !rho)) ||
+  if (!dinr_geometry_valid(geom) || n_ell < 0 || (n_ell > 0 && (!centre || !axes || !rho)) ||
       !out || n < 0)
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid phantom request");
   dinr_ctx tmp;  // holds the temporary allocations and the message

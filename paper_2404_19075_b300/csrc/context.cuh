@@ -73,6 +73,20 @@ struct dinr_ctx {
 };
 
 int dinr_fail(dinr_ctx *c, int status, const char *fmt, ...);
+
+// Whether a geometry description is one the library accepts (the argument
+// checks shared by dinr_create and the phantom projectors).
+inline bool dinr_geometry_valid(const dinr_geometry *g) {
+  if (!g || !g->view_angle || !g->view_time) return false;
+  if (g->beam != DINR_BEAM_PARALLEL && g->beam != DINR_BEAM_CONE) return false;
+  if (g->n_views < 1 || g->det_rows < 1 || g->det_cols < 1) return false;
+  if (!(g->det_pitch_u > 0) || !(g->det_pitch_v > 0) || !(g->fov_r > 0)) return false;
+  if (!(g->fov_z1 > g->fov_z0) || !(g->t1 > g->t0)) return false;
+  if (g->samples_per_ray < 1 || g->samples_per_ray > 4096) return false;
+  if (g->beam == DINR_BEAM_CONE && (!(g->sod > g->fov_r) || !(g->sdd > g->sod))) return false;
+  if (g->subpixels < 0 || g->subpixels > 8) return false;
+  return true;
+}
 void dinr_serve_release(dinr_ctx *c);
 
 // Brackets the launches issued in its scope with two events on the context

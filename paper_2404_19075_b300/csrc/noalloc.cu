@@ -1,14 +1,22 @@
 // dinr_phantom_project_noalloc: the phantom projector for callers that
 // cannot allocate device memory (see include/dinr.h).
 //
-// The per-view table and the ellipsoid parameters that dinr_phantom_project
+// The per-view table and the ellipsoid records that dinr_phantom_project
 // stages in freshly allocated device memory live here in one file-scope
 // device array instead. Host code must not pass the array's name to a
 // kernel (on the host it is only a stand-in symbol); its device address is
-// looked up once per device with cudaGetSymbolAddress and cached.
+// looked up with cudaGetSymbolAddress, with the device current, once per
+// device context, and cached.
+//
+// The table is built on the host (the same FP64 cos, sin and time
+// normalisation as dinr_phantom_project) in a static host buffer, under a
+// mutex, and copied with one cudaMemcpyAsync per part. The buffer is
+// ordinary pageable memory, so each copy has taken its bytes out of it when
+// cudaMemcpyAsync returns; the caller's arrays are read only during the call.
 #include "context.cuh"
 
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 using namespace dinr;
@@ -20,41 +28,50 @@ constexpr int kMaxEll = 1024;
 constexpr int kMaxDevices = 64;
 
 // Layout of the scratch array, in doubles.
-constexpr int kOffAngle = 0;                          // [kMaxViews] raw angles
-constexpr int kOffTime = kOffAngle + kMaxViews;       // [kMaxViews] raw times
-constexpr int kOffCs = kOffTime + kMaxViews;          // [kMaxViews] (cos, sin)
-constexpr int kOffTbar = kOffCs + 2 * kMaxViews;      // [kMaxViews] normalised times
-constexpr int kOffCentre = kOffTbar + kMaxViews;      // [3 kMaxEll]
-constexpr int kOffAxes = kOffCentre + 3 * kMaxEll;    // [3 kMaxEll]
-constexpr int kOffRho = kOffAxes + 3 * kMaxEll;       // [kMaxEll]
-constexpr int kOffVel = kOffRho + kMaxEll;            // [3 kMaxEll]
-constexpr int kOffEll = kOffVel + 3 * kMaxEll;        // [10 kMaxEll] packed ellipsoids
-constexpr int kScratchDoubles = kOffEll + 10 * kMaxEll;  // 40,960 doubles = 320 KiB
+constexpr int kOffCs = 0;                              // [kMaxViews] (cos, sin) of each view
+constexpr int kOffTbar = kOffCs + 2 * kMaxViews;       // [kMaxViews] normalised view times
+constexpr int kOffTime = kOffTbar + kMaxViews;         // [kMaxViews] view times
+constexpr int kOffEll = kOffTime + kMaxViews;          // [10 kMaxEll] packed ellipsoids
+constexpr int kScratchDoubles = kOffEll + 10 * kMaxEll;  // 26,624 doubles = 208 KiB
 
 static __device__ __align__(256) double g_phantom_scratch[kScratchDoubles];
 
-std::mutex g_mu;
-double *g_dev_ptr[kMaxDevices] = {};
+// Host image of the scratch array (pageable), filled under g_mu.
+double g_host_image[kScratchDoubles];
 
-// Per-view (cos, sin, normalised time) in FP64 and the packed ellipsoid
-// records (centre, axes, rho, velocity) that k_phantom reads.
-__global__ void k_prep(int n_views, double t0, double t1, int n_ell, int has_vel, double *s) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_views) {
-    double a = s[kOffAngle + i];
-    s[kOffCs + 2 * i] = cos(a);
-    s[kOffCs + 2 * i + 1] = sin(a);
-    s[kOffTbar + i] = 2.0 * (s[kOffTime + i] - t0) / (t1 - t0) - 1.0;
+std::mutex g_mu;
+struct DevSlot {
+  unsigned long long ctx_id = 0;  // context the address belongs to (0: none yet)
+  double *ptr = nullptr;
+};
+DevSlot g_slot[kMaxDevices];
+
+typedef int (*PfnCtxGetCurrent)(void **ctx);
+typedef int (*PfnCtxGetId)(void *ctx, unsigned long long *id);
+
+// Unique id of the calling thread's current context (0 if there is none or
+// the driver cannot say). A device reset or a new context gets a new id.
+unsigned long long current_ctx_id() {
+  static PfnCtxGetCurrent get_current = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<PfnCtxGetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PfnCtxGetId>(f);
+    looked_up = true;
   }
-  if (i < n_ell) {
-    double *e = s + kOffEll + 10 * i;
-    for (int d = 0; d < 3; ++d) {
-      e[d] = s[kOffCentre + 3 * i + d];
-      e[3 + d] = s[kOffAxes + 3 * i + d];
-      e[7 + d] = has_vel ? s[kOffVel + 3 * i + d] : 0.0;
-    }
-    e[6] = s[kOffRho + i];
-  }
+  if (!get_current || !get_id) return 0;
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
 }
 
 }  // namespace
@@ -65,12 +82,8 @@ dinr_status dinr_phantom_project_noalloc(const dinr_geometry *geom, int n_ell,
                                          const int64_t *idx, int64_t n, float *out,
                                          void *cuda_stream) {
   const dinr_geometry *g = geom;
-  if (!g || !g->view_angle || !g->view_time || n < 0 || !out || n_ell < 0 ||
-      (n_ell > 0 && (!centre || !axes || !rho)) ||
-      (g->beam != DINR_BEAM_PARALLEL && g->beam != DINR_BEAM_CONE) || g->n_views < 1 ||
-      g->det_rows < 1 || g->det_cols < 1 || !(g->det_pitch_u > 0) || !(g->det_pitch_v > 0) ||
-      !(g->fov_r > 0) || !(g->fov_z1 > g->fov_z0) || !(g->t1 > g->t0) ||
-      (g->beam == DINR_BEAM_CONE && (!(g->sod > g->fov_r) || !(g->sdd > g->sod))))
+  if (!dinr_geometry_valid(g) || n < 0 || !out || n_ell < 0 ||
+      (n_ell > 0 && (!centre || !axes || !rho)))
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG, "invalid phantom request");
   if (g->n_views > kMaxViews || n_ell > kMaxEll)
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_ARG,
@@ -83,42 +96,59 @@ dinr_status dinr_phantom_project_noalloc(const dinr_geometry *geom, int n_ell,
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return (dinr_status)dinr_fail(nullptr, DINR_ERR_CUDA, "no usable current device");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int M = g->n_views;
   double *s = nullptr;
+  std::lock_guard<std::mutex> lock(g_mu);
   {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[dev]) {
+    // The address is looked up again when the current context is not the
+    // one it was taken in (a device reset gives the device a new context).
+    const unsigned long long id = current_ctx_id();
+    DevSlot &slot = g_slot[dev];
+    if (!slot.ptr || id == 0 || slot.ctx_id != id) {
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_phantom_scratch);
       if (e != cudaSuccess)
         return (dinr_status)dinr_fail(nullptr, DINR_ERR_CUDA, "cudaGetSymbolAddress: %s",
                                       cudaGetErrorString(e));
-      g_dev_ptr[dev] = static_cast<double *>(p);
+      slot.ptr = static_cast<double *>(p);
+      slot.ctx_id = current_ctx_id();
     }
-    s = g_dev_ptr[dev];
+    s = slot.ptr;
   }
 
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  const size_t d8 = sizeof(double);
-  const int M = g->n_views;
-  struct Copy {
+  // Host image: per view (cos, sin), normalised time and time in FP64 (as
+  // dinr_phantom_project forms them), then the packed ellipsoid records
+  // (centre, semi-axes, rho, velocity) that the phantom kernel reads.
+  double *h = g_host_image;
+  for (int m = 0; m < M; ++m) {
+    h[kOffCs + 2 * m] = std::cos(g->view_angle[m]);
+    h[kOffCs + 2 * m + 1] = std::sin(g->view_angle[m]);
+    h[kOffTbar + m] = 2.0 * (g->view_time[m] - g->t0) / (g->t1 - g->t0) - 1.0;
+    h[kOffTime + m] = g->view_time[m];
+  }
+  for (int k = 0; k < n_ell; ++k) {
+    double *r = h + kOffEll + 10 * k;
+    for (int d = 0; d < 3; ++d) {
+      r[d] = centre[3 * k + d];
+      r[3 + d] = axes[3 * k + d];
+      r[7 + d] = vel ? vel[3 * k + d] : 0.0;
+    }
+    r[6] = rho[k];
+  }
+  struct Part {
     int off;
-    const double *src;
     size_t count;
-  } copies[] = {{kOffAngle, g->view_angle, (size_t)M},
-                {kOffTime, g->view_time, (size_t)M},
-                {kOffCentre, centre, 3 * (size_t)n_ell},
-                {kOffAxes, axes, 3 * (size_t)n_ell},
-                {kOffRho, rho, (size_t)n_ell},
-                {kOffVel, vel, 3 * (size_t)n_ell}};
-  for (const Copy &c : copies) {
-    if (!c.src || c.count == 0) continue;
-    e = cudaMemcpyAsync(s + c.off, c.src, c.count * d8, cudaMemcpyHostToDevice, st);
+  } parts[] = {{kOffCs, 2 * (size_t)M}, {kOffTbar, (size_t)M}, {kOffTime, (size_t)M},
+               {kOffEll, 10 * (size_t)n_ell}};
+  for (const Part &q : parts) {
+    if (q.count == 0) continue;
+    e = cudaMemcpyAsync(s + q.off, h + q.off, q.count * sizeof(double), cudaMemcpyHostToDevice,
+                        st);
     if (e != cudaSuccess)
       return (dinr_status)dinr_fail(nullptr, DINR_ERR_CUDA, "staging copy: %s",
                                     cudaGetErrorString(e));
   }
-  int m = M > n_ell ? M : n_ell;
-  k_prep<<<(m + 127) / 128, 128, 0, st>>>(M, g->t0, g->t1, n_ell, vel ? 1 : 0, s);
 
   GeoDev d{};
   d.beam = g->beam;

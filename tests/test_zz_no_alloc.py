@@ -41,20 +41,25 @@ def _call(fn_name, geometry, phantom, idx):
 
 
 def test_noalloc_matches_allocating_projector_twice():
+    """The larger geometry (512 views, 16 moving ellipsoids) first, then the
+    smaller one (64 views, 3 ellipsoids), then the larger one again: every
+    result must be bitwise the allocating projector's (both build the same
+    FP64 view table on the host and run the same kernel), so that entries
+    left in the shared array by an earlier call would show up."""
     require_gpu()
-    cases = [(wl.workload(1), np.arange(wl.workload(1).geom.n_proj)),
-             (wl.workload(2), wl.ray_subset(wl.workload(2).geom.n_proj, 50000, 3))]
+    w2, w1 = wl.workload(2), wl.workload(1)
+    big = (w2, wl.ray_subset(w2.geom.n_proj, 50000, 3))
+    small = (w1, np.arange(w1.geom.n_proj))
     got = []
-    for w, idx in cases:                           # two calls in a row
+    for w, idx in (big, small, big):               # calls in a row on one stream
         ph = wl.phantom(w)
         a = _call("dinr_phantom_project_noalloc", w.geom, ph, idx)
         b = _call("dinr_phantom_project", w.geom, ph, idx)
         assert np.isfinite(a).all()
         assert_close(a, b, 1e-6, f"workload {w.index}")
+        assert np.array_equal(a, b), f"workload {w.index}: not bitwise the allocating projector"
         got.append(a)
-    # the first result is unaffected by the second call's use of the array
-    w, idx = cases[0]
-    assert_close(got[0], _call("dinr_phantom_project", w.geom, wl.phantom(w), idx), 1e-6, "first")
+    assert np.array_equal(got[0], got[2])
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
@@ -65,3 +70,8 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     w = wl.workload(1)
     with pytest.raises(AssertionError, match="at most 4096 views"):
         _call("dinr_phantom_project_noalloc", g, wl.phantom(w), np.arange(10))
+    # the same geometry checks as the allocating projector
+    bad = wl.parallel_geometry(8, 8, 8, k[:8] * 1e-3, k[:8] / 8, 5000)
+    for fn in ("dinr_phantom_project_noalloc", "dinr_phantom_project"):
+        with pytest.raises(AssertionError, match="invalid phantom request"):
+            _call(fn, bad, wl.phantom(w), np.arange(10))
