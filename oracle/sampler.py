@@ -60,9 +60,18 @@ def permute(x: int, n: int, seed: int, epoch: int) -> int:
     return y
 
 
+def steps_per_epoch(B: int, n: int) -> int:
+    """ceil(n / B) steps of B rays make one epoch over n pixels."""
+    return -(-n // B)
+
+
+def epoch_of(step: int, B: int, n: int) -> int:
+    """The epoch (0-based) that training step `step` (0-based) falls in."""
+    return step // steps_per_epoch(B, n)
+
+
 def minibatch(step: int, B: int, n: int, seed: int) -> np.ndarray:
     """The B indices of training step `step` (0-based)."""
-    spe = -(-n // B)
-    e, j = divmod(step, spe)
+    e, j = divmod(step, steps_per_epoch(B, n))
     return np.array([permute((j * B + b) % n, n, seed, e) for b in range(B)],
                     dtype=np.int64)

@@ -1,19 +1,24 @@
 """GPU parity of the wide network (8 hidden layers of 512, 12 octaves) on the
 cone-beam geometry: the N-tiled BF16 path against the FP64 oracle on a
-64-ray subset (tolerance 2e-2, ReLU decisions taken in BF16 on both sides),
+64-ray subset (tolerance 2e-2 against the plain oracle unless stated, and
+against the oracle with ReLU decisions taken in BF16),
 and activation recomputation on vs off (bitwise equal loss and gradient,
 several passes per step)."""
 import numpy as np
 import pytest
 import torch
 
-from oracle import step as ostep
 from synthetic import workloads as wl
 
-from gpu_util import assert_close, make_model, projections_for, require_gpu, split_grad
+from gpu_util import check_step, make_model, projections_for, require_gpu
 
 pytestmark = pytest.mark.gpu
 TOL = 2e-2
+# Bound against the plain oracle where 2e-2 does not hold: the first-layer
+# weight gradient (measured 2.6 % on a B300, 0.6 % with BF16-taken ReLU
+# decisions; units within BF16 rounding of zero flip, each flip moving a
+# whole delta entry into the gradient sum).
+PLAIN_TOL = {"dW layer 0": 4e-2}
 
 
 @pytest.fixture(scope="module")
@@ -29,15 +34,11 @@ def test_c4_gradient_bf16_vs_oracle(c4):
     w, idx, proj = c4
     sub = idx[:64]
     m, theta, _ = make_model(w, "bf16", proj=proj, batch=64)
-    ref = ostep.loss_and_grad(theta, w.geom, w.net, sub, proj.astype(np.float64), decide="bf16")
-    assert_close(m.predict(sub).cpu().numpy(), ref["p_bar"], TOL, "p_bar")
-    loss, grad = m.loss_grad(sub)
-    assert abs(loss.item() - ref["loss"]) <= TOL * ref["loss"]
-    g = grad.cpu().numpy()
-    for L, ((gw, gb), (ow, ob)) in enumerate(zip(split_grad(g, w.net), split_grad(ref["grad"], w.net))):
-        assert_close(gw, ow, TOL, f"dW layer {L}")
-        assert_close(gb, ob, TOL, f"db layer {L}")
-    m.close()
+    try:
+        check_step(m, w, w.net, theta, sub, proj, "bf16", plain_tol=PLAIN_TOL,
+                   label="workload 4, 64 rays")
+    finally:
+        m.close()
 
 
 def test_c4_recompute_bitwise_equal(c4):

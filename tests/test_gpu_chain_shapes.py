@@ -3,8 +3,8 @@ workloads do not use: one, two or three 64-column chunks per layer (an odd
 count splits unevenly between the two epilogue warps of a lane quadrant),
 layer-0 inputs wider than the hidden layers, every octave count the chain
 is built for, ReLU and Swish, softplus and identity outputs. BF16 p_bar,
-loss and every gradient against the FP64 oracle (2e-2; ReLU decisions in
-BF16 on both sides), on a ragged batch (8,000 samples: 62.5 tiles), and
+loss and every gradient against the FP64 oracle (2e-2; with ReLU against
+the plain oracle and the one with BF16-taken ReLU decisions), on a ragged batch (8,000 samples: 62.5 tiles), and
 the profile shows that both chains ran."""
 from dataclasses import replace
 
@@ -33,8 +33,7 @@ def test_chain_shapes(W, H, F, act, out_act):
                                 params=wl.he_init(net, w.seeds["weights"]))
     try:
         m.profile(True)
-        check_step(m, w, net, theta, idx, proj, "bf16",
-                   decide="bf16" if act == "relu" else None)
+        check_step(m, w, net, theta, idx, proj, "bf16", label=f"chain {H}x{W} F={F} {act}")
         m.profile(False)
         report = m.profile_report()
         assert "tc_fwd_chain" in report and "tc_bwd_chain" in report

@@ -8,10 +8,10 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import geometry, step as ostep
+from oracle import geometry
 from synthetic import workloads as wl
 
-from gpu_util import assert_close, make_model, projections_for, require_gpu
+from gpu_util import gate_tensors, make_model, oracle_refs, projections_for, require_gpu
 
 pytestmark = pytest.mark.gpu
 TOL = {"fp32": 1e-5, "bf16": 2e-2}
@@ -49,14 +49,13 @@ def test_empty_rays(cone, prec):
     assert torch.count_nonzero(grad) == 0
     assert abs(loss.item() - 0.25 ** 2) <= 1e-7
     mix = np.concatenate([full[:32], empty, full[32:]])
-    ref = ostep.loss_and_grad(theta, w.geom, w.net, mix, proj.astype(np.float64),
-                              decide="bf16" if prec == "bf16" else None)
+    plain, decided = oracle_refs(theta, w.geom, w.net, mix, proj, prec)
     p = m.predict(mix).cpu().numpy()
     assert (p[32:32 + len(empty)] == 0).all()
-    assert_close(p, ref["p_bar"], TOL[prec], "p_bar")
     loss, grad = m.loss_grad(mix)
-    assert abs(loss.item() - ref["loss"]) <= TOL[prec] * ref["loss"]
-    assert_close(grad.cpu().numpy(), ref["grad"], TOL[prec], "grad")
+    assert abs(loss.item() - plain["loss"]) <= TOL[prec] * plain["loss"]
+    got = {"p_bar": p, "grad": grad.cpu().numpy()}
+    gate_tensors(f"empty and full rays {prec}", got, plain, decided, TOL[prec])
     m.close()
 
 
@@ -65,10 +64,9 @@ def test_single_full_and_single_empty_ray(cone, prec):
     w, empty, full, proj = cone
     m, theta, _ = make_model(w, prec, proj=proj, batch=256)
     for sub in (full[:1], empty[:1], np.array([full[0], empty[0]])):
-        ref = ostep.loss_and_grad(theta, w.geom, w.net, sub, proj.astype(np.float64),
-                                  decide="bf16" if prec == "bf16" else None)
+        ref, decided = oracle_refs(theta, w.geom, w.net, sub, proj, prec)
         p = m.predict(sub).cpu().numpy().astype(np.float64)
-        assert_close(p, ref["p_bar"], TOL[prec], f"p_bar n={len(sub)}")
+        gate_tensors(f"single rays {prec}", {"p_bar": p}, ref, decided, TOL[prec])
         loss, grad = m.loss_grad(sub)
         # the loss of one or two rays is (p_bar - p)^2 with cancellation in
         # the difference, so the tolerance is held on p_bar above; the loss
@@ -81,6 +79,6 @@ def test_single_full_and_single_empty_ray(cone, prec):
             assert torch.count_nonzero(grad) == 0
         else:
             # one ray of 256 samples: the per-ray tolerance of the BF16 path
-            assert_close(grad.cpu().numpy(), ref["grad"], TOL[prec] if prec == "fp32" else 5e-2,
-                         f"grad n={len(sub)}")
+            gate_tensors(f"single rays {prec} n={len(sub)}", {"grad": grad.cpu().numpy()}, ref,
+                         decided, TOL[prec] if prec == "fp32" else 5e-2)
     m.close()

@@ -2,8 +2,9 @@
 whole minibatch of a workload (65,536 rays at the workload's samples per
 ray, through its network, in one call of the library) is predicted, and the
 FP64 oracle recomputes the prediction of a seeded sample of those rays one
-by one (ReLU decisions taken on the BF16-rounded forward, as the BF16 path
-takes them). Workloads: the parallel-beam benchmark (2), the cone-beam
+by one (with ReLU, against the plain oracle and against the oracle with its
+ReLU decisions taken on the BF16-rounded forward, as the BF16 path takes
+them). Workloads: the parallel-beam benchmark (2), the cone-beam
 network (3), the paper's network (6) and the paper's network with its
 sub-pixel forward model (8). BF16 tolerance 2e-2."""
 import numpy as np
@@ -14,7 +15,7 @@ from oracle import network as onet
 from oracle import step as ostep
 from synthetic import workloads as wl
 
-from gpu_util import assert_close, make_model, require_gpu
+from gpu_util import assert_close, make_model, plain_gate, require_gpu
 
 pytestmark = pytest.mark.gpu
 TOL = 2e-2
@@ -47,5 +48,11 @@ def test_full_batch_sampled_rays_match_oracle(c):
         m.close()
     assert p.shape == (B,) and np.isfinite(p).all()
     pick = np.sort(np.random.default_rng(22).choice(B, 96, replace=False))
-    ref = oracle_p_bar(theta, w.geom, w.net, idx[pick], w.net.act == "relu")
-    assert_close(p[pick], ref, TOL, f"p_bar of sampled rays, workload {c}")
+    plain = oracle_p_bar(theta, w.geom, w.net, idx[pick], False)
+    if w.net.act == "relu":
+        decided = oracle_p_bar(theta, w.geom, w.net, idx[pick], True)
+        assert_close(p[pick], decided, TOL, f"p_bar of sampled rays, workload {c} (BF16-decided)")
+        plain_gate(f"full batch, workload {c}", "p_bar of sampled rays", p[pick], plain, TOL,
+                   decided)
+    else:
+        assert_close(p[pick], plain, TOL, f"p_bar of sampled rays, workload {c}")

@@ -1,10 +1,13 @@
 """The largest shapes the ABI accepts: 4,096 samples per ray, 32 hidden
 layers with 16 octaves, and 8 x 8 sub-pixel rays per pixel (App. A), in
-both precisions, against the FP64 oracle (FP32 1e-5, BF16 2e-2 with ReLU
-decisions in BF16 on both sides). BF16 rounding of every layer's inputs
+both precisions, against the FP64 oracle (FP32 1e-5, BF16 2e-2, with ReLU
+against the plain oracle and the one with BF16-taken ReLU decisions). BF16 rounding of every layer's inputs
 compounds with depth (about sqrt(H) times one layer's); at 32 layers the
 BF16 bound is 2e-2 sqrt(32 / 8) = 4e-2, the depth of the workloads being 8
-at most."""
+at most. Against the plain oracle the 32-layer gradients are held to 1e-1:
+ReLU decisions that flip under BF16 rounding compound over 32 layers
+(measured 7.0 % norm-wise, 7.6 % element-wise on a B300; 0.5 % and 0.8 %
+with BF16-taken decisions)."""
 from dataclasses import replace
 
 import pytest
@@ -16,13 +19,12 @@ from gpu_util import check_step, make_model, require_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _run(w, net, n, prec, seed, tol=None):
+def _run(w, net, n, prec, seed, tol=None, plain_tol=None, label=""):
     idx = wl.ray_subset(w.geom.n_proj, n, seed)
     m, theta, proj = make_model(w, prec, idx=idx, net=net, batch=n,
                                 params=wl.he_init(net, w.seeds["weights"]))
     try:
-        check_step(m, w, net, theta, idx, proj, prec,
-                   decide="bf16" if prec == "bf16" and net.act == "relu" else None, tol=tol)
+        check_step(m, w, net, theta, idx, proj, prec, tol=tol, plain_tol=plain_tol, label=label)
     finally:
         m.close()
 
@@ -32,7 +34,7 @@ def test_4096_samples_per_ray(prec):
     require_gpu()
     w = wl.workload(1)
     w = replace(w, geom=replace(w.geom, samples_per_ray=4096))
-    _run(w, w.net, 12, prec, 51)
+    _run(w, w.net, 12, prec, 51, label="4096 samples per ray")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -41,7 +43,8 @@ def test_32_layers_16_octaves(prec):
     w = wl.workload(1)
     net = replace(w.net, hidden_layers=32, width=32, n_freq=16, act="relu",
                   out_act="identity")
-    _run(w, net, 64, prec, 53, tol=4e-2 if prec == "bf16" else None)
+    _run(w, net, 64, prec, 53, tol=4e-2 if prec == "bf16" else None,
+         plain_tol=1e-1 if prec == "bf16" else None, label="32x32 F=16")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -49,4 +52,4 @@ def test_8x8_subpixel_rays(prec):
     require_gpu()
     w = wl.workload(9)
     w = replace(w, geom=replace(w.geom, subpixels=8))
-    _run(w, w.net, 12, prec, 57)
+    _run(w, w.net, 12, prec, 57, label="8x8 sub-pixel rays")

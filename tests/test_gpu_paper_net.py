@@ -36,7 +36,7 @@ def test_grff_relu_fused_chain():
     m, theta, proj = make_model(w, "bf16", idx=idx, net=net,
                                 params=wl.he_init(net, w.seeds["weights"]))
     m.profile(True)
-    check_step(m, w, net, theta, idx, proj, "bf16", decide="bf16")
+    check_step(m, w, net, theta, idx, proj, "bf16", label="GRFF relu")
     m.profile(False)
     assert "tc_fwd_chain" in m.profile_report()
     pts = np.random.default_rng(3).uniform(-0.9, 0.9, (300, 4))

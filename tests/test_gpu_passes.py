@@ -1,7 +1,8 @@
 """Steps split into several passes (the workspace holds fewer rays than the
 minibatch): the fused chains over four passes and the App. A forward model
 with the unfused wide network and activation recomputation, against the
-FP64 oracle (BF16 2e-2; ReLU decisions in BF16 on both sides), and
+FP64 oracle (BF16 2e-2, against the plain oracle and the one with
+BF16-taken ReLU decisions), and
 recomputation on vs off bitwise equal on the App. A model."""
 from dataclasses import replace
 
@@ -22,7 +23,7 @@ def test_chains_over_four_passes():
     m, theta, proj = make_model(w, "bf16", idx=idx, batch=1024, chunk=300)
     try:
         m.profile(True)
-        check_step(m, w, w.net, theta, idx, proj, "bf16", decide="bf16")
+        check_step(m, w, w.net, theta, idx, proj, "bf16", label="passes chains")
         m.profile(False)
         assert m.profile_report()["tc_fwd_chain"]["launches"] >= 4
     finally:
@@ -43,7 +44,7 @@ def test_subpixel_wide_network_recompute():
         try:
             if rc == 1:
                 m.profile(True)
-                check_step(m, w, net, theta, idx, proj, "bf16", decide="bf16")
+                check_step(m, w, net, theta, idx, proj, "bf16", label="passes App. A wide")
                 m.profile(False)
                 assert m.profile_report()["tc_fwd_recompute"]["launches"] > 0
             loss, grad = m.loss_grad(idx)

@@ -1,35 +1,27 @@
 """GPU parity of the paper's forward model (App. A: D x D sub-pixel rays per
 pixel, a variable number of samples per ray, p_bar over all of a pixel's
 samples) against the FP64 oracle: the FP32 path (1e-5), the BF16 unfused
-path and the fused chains (2e-2; ReLU decisions in BF16 where ReLU is
-used), predictions of pixels whose rays all miss the field of view, and the
-full-size paper network on a subset of pixels."""
+path and the fused chains (2e-2; with ReLU against the plain oracle and
+the one with BF16-taken ReLU decisions), predictions of pixels whose rays
+all miss the field of view, and the full-size paper network on a subset of
+pixels."""
 from dataclasses import replace
 
 import numpy as np
 import pytest
 
-from oracle import geometry, step as ostep
+from oracle import geometry
 from synthetic import workloads as wl
 
-from gpu_util import assert_close, make_model, projections_for, require_gpu, split_grad
+from gpu_util import (assert_close, check_step, make_model, oracle_refs, plain_gate,
+                      require_gpu)
 
 pytestmark = pytest.mark.gpu
 TOL = {"fp32": 1e-5, "bf16": 2e-2}
 
 
-def _check(m, w, geom, net, theta, idx, proj, prec, decide=None):
-    ref = ostep.loss_and_grad(theta, geom, net, idx, proj.astype(np.float64), decide=decide)
-    assert_close(m.predict(idx).cpu().numpy(), ref["p_bar"], TOL[prec], "p_bar")
-    loss, grad = m.loss_grad(idx)
-    assert abs(loss.item() - ref["loss"]) <= TOL[prec] * ref["loss"]
-    g = grad.cpu().numpy()
-    pairs = list(zip(split_grad(g, net), split_grad(ref["grad"], net)))
-    for L, ((gw, gb), (ow, ob)) in enumerate(pairs[:-1]):
-        assert_close(gw, ow, TOL[prec], f"dW layer {L}")
-        assert_close(gb, ob, TOL[prec], f"db layer {L}")
-    (gw, gb), (ow, ob) = pairs[-1]
-    assert_close(np.concatenate([gw, gb]), np.concatenate([ow, ob]), TOL[prec], "output layer")
+def _check(m, w, geom, net, theta, idx, proj, prec, label):
+    check_step(m, replace(w, geom=geom), net, theta, idx, proj, prec, label=label)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -38,7 +30,7 @@ def test_subpixel_model_parity_size(prec):
     w = wl.workload(9)
     idx = wl.ray_subset(w.geom.n_proj, 512, w.seeds["sampler"])
     m, theta, proj = make_model(w, prec, idx=idx, batch=512, chunk=200)   # three passes
-    _check(m, w, w.geom, w.net, theta, idx, proj, prec)
+    _check(m, w, w.geom, w.net, theta, idx, proj, prec, "App. A parity size")
     m.close()
 
 
@@ -53,7 +45,7 @@ def test_subpixel_model_fused_chains(act, out_act, C, F):
     m, theta, proj = make_model(w, "bf16", idx=idx, net=net, batch=384,
                                 params=wl.he_init(net, w.seeds["weights"]))
     m.profile(True)
-    _check(m, w, w.geom, net, theta, idx, proj, "bf16", decide="bf16" if act == "relu" else None)
+    _check(m, w, w.geom, net, theta, idx, proj, "bf16", f"App. A chains {act}")
     m.profile(False)
     assert "tc_fwd_chain" in m.profile_report()
     m.close()
@@ -72,8 +64,9 @@ def test_subpixel_pixels_outside_the_fov():
     m, theta, proj = make_model(w, "bf16", idx=both, geom=g, batch=64)
     p = m.predict(both).cpu().numpy()
     assert (p[:len(idx)] == 0).all()
-    ref = ostep.loss_and_grad(theta, g, w.net, both, proj.astype(np.float64), decide="bf16")
-    assert_close(p, ref["p_bar"], TOL["bf16"], "p_bar")
+    plain, decided = oracle_refs(theta, g, w.net, both, proj, "bf16")
+    assert_close(p, decided["p_bar"], TOL["bf16"], "p_bar (BF16-decided oracle)")
+    plain_gate("App. A outside the FOV", "p_bar", p, plain["p_bar"], TOL["bf16"], decided["p_bar"])
     m.close()
 
 
@@ -83,7 +76,7 @@ def test_subpixel_paper_network_full_size_subset(prec, n):
     w = wl.workload(8)
     idx = wl.ray_subset(w.geom.n_proj, n, 808)
     m, theta, proj = make_model(w, prec, idx=idx, batch=64)
-    _check(m, w, w.geom, w.net, theta, idx, proj, prec)
+    _check(m, w, w.geom, w.net, theta, idx, proj, prec, "App. A workload 8 subset")
     m.close()
 
 
@@ -106,7 +99,6 @@ def test_subpixel_cone_beam(prec, act, C, F):
     m, theta, proj = make_model(w, prec, idx=idx, net=net, batch=256,
                                 params=wl.he_init(net, w.seeds["weights"]))
     try:
-        _check(m, w, geom, net, theta, idx, proj, prec,
-               decide="bf16" if act == "relu" else None)
+        _check(m, w, geom, net, theta, idx, proj, prec, f"App. A cone {act}")
     finally:
         m.close()

@@ -2,7 +2,8 @@
 fused chains do not take: widths that are not whole 64-column chunks (96,
 224) and wide layers split into three or four 256-column N tiles (768,
 1024), with ReLU and Swish. BF16 p_bar, loss and every gradient against the
-FP64 oracle (2e-2; ReLU decisions in BF16 on both sides) on a ragged batch
+FP64 oracle (2e-2; with ReLU against the plain oracle and the one with
+BF16-taken ReLU decisions) on a ragged batch
 (8,000 samples), and the profile shows the per-layer GEMMs ran."""
 from dataclasses import replace
 
@@ -30,8 +31,7 @@ def test_unfused_shapes(W, H, F, act, out_act):
                                 params=wl.he_init(net, w.seeds["weights"]))
     try:
         m.profile(True)
-        check_step(m, w, net, theta, idx, proj, "bf16",
-                   decide="bf16" if act == "relu" else None)
+        check_step(m, w, net, theta, idx, proj, "bf16", label=f"unfused {H}x{W} F={F} {act}")
         m.profile(False)
         report = m.profile_report()
         assert "tc_fwd" in report and "tc_dw" in report and "tc_fwd_chain" not in report
