@@ -209,6 +209,30 @@ DINR_API dinr_status dinr_train_step(dinr_ctx *ctx, const int64_t *ray_idx, int 
 DINR_API dinr_status dinr_loss_grad(dinr_ctx *ctx, const int64_t *ray_idx, int n,
                            int idx_on_device, float *loss_dev, float *grad_dev);
 
+/* dinr_loss_grad in two halves, for an autograd function whose backward
+ * runs only when a gradient is asked for (Eq. 1-5 forward; App. A
+ * gradient "partiald" backward).
+ * dinr_forward: stages the minibatch (indices as in dinr_train_step), runs
+ * the forward model and the loss (Eq. 5) and writes L to loss_dev (device
+ * float[1], or NULL). It launches no backward kernel. When the minibatch is
+ * one pass of the workspace (n <= chunk_rays), the activations the backward
+ * needs stay in the workspace; otherwise only the loss is kept.
+ * dinr_backward: the gradient of dloss * L for the minibatch of the last
+ * dinr_forward, into the context's gradient (dinr_get_grads) and, when
+ * grad_dev is not NULL, device float[dinr_param_count]. dloss_dev: device
+ * float[1] (the upstream factor), or NULL for 1. It runs the adjoint
+ * kernels on the kept activations, or, when none were kept (several
+ * passes, or the workspace was used since), the whole step again with the
+ * same indices and parameters (the same result).
+ * Errors: DINR_ERR_ARG from dinr_backward when there is no minibatch to
+ * differentiate: no dinr_forward yet, or since it another call restaged
+ * indices (train_step, loss_grad, predict) or changed the parameters
+ * (set_params, set_state, an Adam step). Asynchronous on the context
+ * stream; errors otherwise as dinr_loss_grad. */
+DINR_API dinr_status dinr_forward(dinr_ctx *ctx, const int64_t *ray_idx, int n,
+                                  int idx_on_device, float *loss_dev);
+DINR_API dinr_status dinr_backward(dinr_ctx *ctx, const float *dloss_dev, float *grad_dev);
+
 /* Forward model only (Eq. 1, 2): p_bar for n rays into device float[n]. */
 DINR_API dinr_status dinr_predict(dinr_ctx *ctx, const int64_t *ray_idx, int n,
                          int idx_on_device, float *pbar_dev);

@@ -341,6 +341,8 @@ dinr_status dinr_set_projections(dinr_ctx *c, const float *proj, int on_device) 
 static dinr_status stage_indices(dinr_ctx *c, const int64_t *idx, int n, int on_device) {
   if (n < 1 || n > c->batch_rays)
     return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "n = %d outside [1, %d]", n, c->batch_rays);
+  c->fwd_n = 0;  // the minibatch a dinr_forward left is replaced
+  c->fwd_kept = false;
   if (!idx) {
     launch_sample_indices(c->n_proj, n, c->step, c->sampler_seed, c->d_idx, c->st);
     CKL();
@@ -381,6 +383,37 @@ dinr_status dinr_loss_grad(dinr_ctx *c, const int64_t *idx, int n, int on_device
   if (s != DINR_OK) return s;
   if (loss_dev)
     CK(cudaMemcpyAsync(loss_dev, c->d_loss, sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+  if (grad_dev)
+    CK(cudaMemcpyAsync(grad_dev, c->d_grad, sizeof(float) * c->P, cudaMemcpyDeviceToDevice,
+                       c->st));
+  return DINR_OK;
+}
+
+dinr_status dinr_forward(dinr_ctx *c, const int64_t *idx, int n, int on_device,
+                         float *loss_dev) {
+  LIVE(c);
+  dinr_status s = stage_indices(c, idx, n, on_device);
+  if (s != DINR_OK) return s;
+  s = run_loss_grad(c, n, kLossOnly);
+  if (s != DINR_OK) return s;
+  c->fwd_n = n;
+  if (loss_dev)
+    CK(cudaMemcpyAsync(loss_dev, c->d_loss, sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+  return DINR_OK;
+}
+
+dinr_status dinr_backward(dinr_ctx *c, const float *dloss_dev, float *grad_dev) {
+  LIVE(c);
+  if (c->fwd_n < 1)
+    return (dinr_status)dinr_fail(c, DINR_ERR_ARG,
+                                  "dinr_backward: no dinr_forward minibatch to differentiate");
+  // the kept activations of a one-pass forward, else the whole step again
+  dinr_status s = run_loss_grad(c, c->fwd_n, c->fwd_kept ? kGradOnly : kLossGrad);
+  if (s != DINR_OK) return s;
+  if (dloss_dev) {
+    launch_scale_by(c->d_grad, c->P, dloss_dev, c->d_grad, c->st);
+    CKL();
+  }
   if (grad_dev)
     CK(cudaMemcpyAsync(grad_dev, c->d_grad, sizeof(float) * c->P, cudaMemcpyDeviceToDevice,
                        c->st));

@@ -45,6 +45,14 @@ struct dinr_ctx {
   uint64_t sampler_seed = 0;
   long long step = 0;  // completed Adam steps
 
+  // The minibatch of the last dinr_forward, left for dinr_backward: its
+  // rays (0: none; restaging the indices clears it) and, when the step fit
+  // in one pass, its samples with the activations still in the workspace
+  // (any other use of the workspace clears fwd_kept).
+  int fwd_n = 0;
+  bool fwd_kept = false;
+  long long fwd_ns = 0;
+
   // FP32 workspace (per pass of chunk_rays rays)
   float *E = nullptr, *Z = nullptr, *D0 = nullptr, *D1 = nullptr;
   float *zout = nullptr, *dz = nullptr;
@@ -106,8 +114,14 @@ long long workspace_bytes_per_sample(const dinr_ctx *c);
 bool recompute_applies(const dinr_ctx *c);
 dinr_status alloc_workspace(dinr_ctx *c);
 void destroy_backend(dinr_ctx *c);
-// Loss into d_loss and gradient into d_grad for the n staged rays in d_idx.
-dinr_status run_loss_grad(dinr_ctx *c, int n);
+// What a loss-and-gradient run of the n staged rays in d_idx does:
+// kLossGrad loss into d_loss and gradient into d_grad (every pass forward
+// then backward); kLossOnly the forward and loss only, keeping the
+// activations when the minibatch is one pass (fwd_kept, fwd_ns); kGradOnly
+// the backward of the kept pass (callers recompute with kLossGrad when
+// nothing was kept).
+enum RunMode { kLossGrad = 0, kLossOnly = 1, kGradOnly = 2 };
+dinr_status run_loss_grad(dinr_ctx *c, int n, RunMode mode = kLossGrad);
 // Forward model p_bar for n_rays rays of a source, S samples each, into out.
 dinr_status run_forward_rays(dinr_ctx *c, const dinr::SourceArgs &src, long long n_rays, int S,
                              float *out);

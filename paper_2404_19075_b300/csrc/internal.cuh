@@ -139,6 +139,9 @@ void launch_loss_sum(const float *sq, long long n, float inv_B, float *loss, boo
                      cudaStream_t st);
 
 // Adam (Kingma & Ba), FP32 master weights.
+// out = g * (*scale) over P floats (scale: device float[1]).
+void launch_scale_by(const float *g, long long P, const float *scale, float *out,
+                     cudaStream_t st);
 void launch_adam(float *theta, float *m, float *v, const float *g, long long P, float lr,
                  float beta1, float beta2, float eps, float bc1, float bc2, cudaStream_t st);
 

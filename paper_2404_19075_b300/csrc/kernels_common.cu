@@ -515,4 +515,16 @@ void launch_adam(float *theta, float *m, float *v, const float *g, long long P, 
   k_adam<<<ceil_div(P, 256), 256, 0, st>>>(theta, m, v, g, P, lr, beta1, beta2, eps, bc1, bc2);
 }
 
+
+// out[i] = g[i] * (*scale): the gradient of (scale x L) from that of L (the
+// upstream factor an autograd backward passes in).
+__global__ void k_scale_by(const float *g, long long P, const float *scale, float *out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < P) out[i] = g[i] * scale[0];
+}
+void launch_scale_by(const float *g, long long P, const float *scale, float *out,
+                     cudaStream_t st) {
+  k_scale_by<<<ceil_div(P, 256), 256, 0, st>>>(g, P, scale, out);
+}
+
 }  // namespace dinr

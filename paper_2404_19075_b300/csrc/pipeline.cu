@@ -92,6 +92,8 @@ dinr_status backend_poll(dinr_ctx *c) {
 }
 
 dinr_status after_param_update(dinr_ctx *c) {
+  c->fwd_n = 0;  // a forward taken with the old parameters has no backward now
+  c->fwd_kept = false;
   if (c->prec != DINR_PREC_FP32) return tc_params_changed(c);
   return DINR_OK;
 }
@@ -243,7 +245,13 @@ static dinr_status f32_subpix_pass(dinr_ctx *c, const long long *idx, int nr, fl
                        train ? c->dz : nullptr);
 }
 
-static dinr_status f32_loss_grad(dinr_ctx *c, int n) {
+static dinr_status f32_loss_grad(dinr_ctx *c, int n, RunMode mode) {
+  if (mode == kGradOnly) {
+    dinr_status s = f32_backward(c, c->fwd_ns, false);
+    c->fwd_kept = false;
+    return s;
+  }
+  const bool one_pass = n <= c->chunk_rays;
   float inv_B = 1.0f / (float)n;
   for (int r0 = 0, pass = 0; r0 < n; r0 += c->chunk_rays, ++pass) {
     int nr = n - r0 < c->chunk_rays ? n - r0 : c->chunk_rays;
@@ -254,30 +262,35 @@ static dinr_status f32_loss_grad(dinr_ctx *c, int n) {
       launch_loss_sum(c->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
       CKL();
       if (c->prof) c->samples_done += ns;
-      s = f32_backward(c, ns, pass > 0);
+    } else {
+      SourceArgs src{};
+      src.kind = kSrcTrainRays;
+      src.idx = c->d_idx + r0;
+      {
+        ProfScope ps(c, "encode", 0.0, 4.0 * ns * c->ldE);
+        launch_encode_f32(c->geo, src, nr, c->S, c->F, c->grff_c, c->d_grff_B, c->ldE, c->E,
+                          c->ray_l, c->d_proj, c->ray_p, c->st);
+        CKL();
+      }
+      dinr_status s = f32_hidden(c, ns);
       if (s != DINR_OK) return s;
+      launch_out_segsum_f32(zlast(c, ns), c->W, c->W, c->act, c->out_act,
+                            c->d_params + c->offW[c->H], c->d_params + c->offb[c->H], nr, c->S,
+                            c->mu0, c->ray_l, c->ray_p, inv_B, true, c->zout, c->pbar, c->sq,
+                            c->dz, c->st);
+      CKL();
+      launch_loss_sum(c->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
+      CKL();
+      if (c->prof) c->samples_done += ns;
+    }
+    if (mode == kLossOnly) {
+      if (one_pass) {
+        c->fwd_kept = true;
+        c->fwd_ns = ns;
+      }
       continue;
     }
-    SourceArgs src{};
-    src.kind = kSrcTrainRays;
-    src.idx = c->d_idx + r0;
-    {
-      ProfScope ps(c, "encode", 0.0, 4.0 * ns * c->ldE);
-      launch_encode_f32(c->geo, src, nr, c->S, c->F, c->grff_c, c->d_grff_B, c->ldE, c->E,
-                        c->ray_l, c->d_proj, c->ray_p, c->st);
-      CKL();
-    }
-    dinr_status s = f32_hidden(c, ns);
-    if (s != DINR_OK) return s;
-    launch_out_segsum_f32(zlast(c, ns), c->W, c->W, c->act, c->out_act,
-                          c->d_params + c->offW[c->H], c->d_params + c->offb[c->H], nr, c->S,
-                          c->mu0, c->ray_l, c->ray_p, inv_B, true, c->zout, c->pbar, c->sq, c->dz,
-                          c->st);
-    CKL();
-    launch_loss_sum(c->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
-    CKL();
-    if (c->prof) c->samples_done += ns;
-      s = f32_backward(c, ns, pass > 0);
+    dinr_status s = f32_backward(c, ns, pass > 0);
     if (s != DINR_OK) return s;
   }
   return DINR_OK;
@@ -321,18 +334,21 @@ static dinr_status f32_forward(dinr_ctx *c, const SourceArgs &src0, long long n_
 
 // ------------------------------------------------------------ dispatch
 
-dinr_status run_loss_grad(dinr_ctx *c, int n) {
-  if (c->prec != DINR_PREC_FP32) return tc_loss_grad(c, n);
-  return f32_loss_grad(c, n);
+dinr_status run_loss_grad(dinr_ctx *c, int n, RunMode mode) {
+  if (mode != kGradOnly) c->fwd_kept = false;
+  if (c->prec != DINR_PREC_FP32) return tc_loss_grad(c, n, mode);
+  return f32_loss_grad(c, n, mode);
 }
 
 dinr_status run_forward_rays(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S,
                              float *out) {
+  c->fwd_kept = false;
   if (c->prec != DINR_PREC_FP32) return tc_forward_rays(c, src, n_rays, S, out);
   return f32_forward(c, src, n_rays, S, out);
 }
 
 dinr_status run_forward_points(dinr_ctx *c, const SourceArgs &src, long long n, float *out) {
+  c->fwd_kept = false;
   if (c->prec != DINR_PREC_FP32) return tc_forward_points(c, src, n, out);
   return f32_forward(c, src, n, 1, out);
 }

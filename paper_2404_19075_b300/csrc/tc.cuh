@@ -9,7 +9,7 @@ bool tc_recompute_applies(const dinr_ctx *c);
 dinr_status tc_alloc(dinr_ctx *c);
 void tc_destroy(dinr_ctx *c);
 dinr_status tc_params_changed(dinr_ctx *c);
-dinr_status tc_loss_grad(dinr_ctx *c, int n);
+dinr_status tc_loss_grad(dinr_ctx *c, int n, RunMode mode);
 dinr_status tc_forward_rays(dinr_ctx *c, const dinr::SourceArgs &src, long long n_rays, int S,
                             float *out);
 dinr_status tc_forward_points(dinr_ctx *c, const dinr::SourceArgs &src, long long n, float *out);

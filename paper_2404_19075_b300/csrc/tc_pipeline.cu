@@ -816,50 +816,65 @@ static dinr_status subpix_outputs(dinr_ctx *c, long long ns, bool store_h) {
   return forward(c, ns);
 }
 
-dinr_status tc_loss_grad(dinr_ctx *c, int n) {
+dinr_status tc_loss_grad(dinr_ctx *c, int n, RunMode mode) {
   TcState *t = S_(c);
+  if (mode == kGradOnly) {
+    dinr_status s = backward(c, c->fwd_ns, false);
+    c->fwd_kept = false;
+    if (s == DINR_OK && t->fp8) {
+      k_fp8_scales<<<1, 32, 0, c->st>>>(t->amax_h, t->fscale + 1 + c->H, c->H);
+      CKL();
+    }
+    return s;
+  }
+  const bool one_pass = n <= c->chunk_rays;
+  // a forward whose backward comes later stores its activations only when
+  // they stay in the workspace (one pass); otherwise the backward recomputes
+  const bool store = mode == kLossGrad || one_pass;
   float inv_B = 1.0f / (float)n;
   for (int r0 = 0, pass = 0; r0 < n; r0 += c->chunk_rays, ++pass) {
     int nr = n - r0 < c->chunk_rays ? n - r0 : c->chunk_rays;
     long long ns = (long long)nr * c->S;
     if (c->geo.D > 0) {
       dinr_status s = subpix_setup(c, c->d_idx + r0, nr, c->d_proj, &ns);
-      if (s == DINR_OK) s = subpix_outputs(c, ns, true);
+      if (s == DINR_OK) s = subpix_outputs(c, ns, store);
       if (s == DINR_OK) s = subpix_segsum(c, t->zout, nr, inv_B, true, t->pbar, t->sq, t->dz);
       if (s != DINR_OK) return s;
-      launch_loss_sum(t->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
-      CKL();
-      if (c->prof) c->samples_done += ns;
-      s = backward(c, ns, pass > 0);
-      if (s != DINR_OK) return s;
-      continue;
-    }
-    SourceArgs src{};
-    src.kind = kSrcTrainRays;
-    src.idx = c->d_idx + r0;
-    dinr_status s;
-    if (chain_ok(c)) {
-      s = chain(c, src, nr, c->S, true, c->d_proj);
     } else {
-      {
-        ProfScope ps(c, "encode", 0.0, 2.0 * ns * c->ldE);
-        launch_encode_bf16(c->geo, src, nr, c->S, c->F, c->grff_c, c->d_grff_B, c->ldE, t->E,
-                           t->ray_l, c->d_proj, t->ray_p, c->st);
-        CKL();
+      SourceArgs src{};
+      src.kind = kSrcTrainRays;
+      src.idx = c->d_idx + r0;
+      dinr_status s;
+      if (chain_ok(c)) {
+        s = chain(c, src, nr, c->S, store, c->d_proj);
+      } else {
+        {
+          ProfScope ps(c, "encode", 0.0, 2.0 * ns * c->ldE);
+          launch_encode_bf16(c->geo, src, nr, c->S, c->F, c->grff_c, c->d_grff_B, c->ldE, t->E,
+                             t->ray_l, c->d_proj, t->ray_p, c->st);
+          CKL();
+        }
+        s = forward(c, ns);
       }
-      s = forward(c, ns);
+      if (s != DINR_OK) return s;
+      launch_segsum(t->zout, c->out_act, nr, c->S, c->mu0, t->ray_l, t->ray_p, inv_B, true,
+                    t->pbar, t->sq, t->dz, c->st);
+      CKL();
     }
-    if (s != DINR_OK) return s;
-    launch_segsum(t->zout, c->out_act, nr, c->S, c->mu0, t->ray_l, t->ray_p, inv_B, true,
-                  t->pbar, t->sq, t->dz, c->st);
-    CKL();
     launch_loss_sum(t->sq, nr, inv_B, c->d_loss, pass > 0, c->st);
     CKL();
     if (c->prof) c->samples_done += ns;
-      s = backward(c, ns, pass > 0);
+    if (mode == kLossOnly) {
+      if (one_pass) {
+        c->fwd_kept = true;
+        c->fwd_ns = ns;
+      }
+      continue;
+    }
+    dinr_status s = backward(c, ns, pass > 0);
     if (s != DINR_OK) return s;
   }
-  if (t->fp8) {
+  if (t->fp8 && mode == kLossGrad) {
     k_fp8_scales<<<1, 32, 0, c->st>>>(t->amax_h, t->fscale + 1 + c->H, c->H);
     CKL();
   }
@@ -955,6 +970,7 @@ bool tc_serve_backend(dinr_ctx *c, ServeBackend *b) {
 
 dinr_status tc_serve_chain(dinr_ctx *c, const WorkItem *items, const int *tile_item,
                            long long m_tiles) {
+  c->fwd_kept = false;  // the batch overwrites the workspace
   TcState *t = S_(c);
   ChainMaps maps;
   memset(&maps, 0, sizeof(maps));

@@ -163,6 +163,25 @@ class Dinr:
         self._c(_abi.lib().dinr_loss_grad(self._h, _ptr(t), n, on_dev, _ptr(loss), _ptr(grad)))
         return loss, grad
 
+    def forward_loss(self, idx=None, n=None):
+        """The loss of a minibatch (CUDA tensor [1]) from the forward model
+        alone; the backward is left for backward_grad."""
+        t, m, on_dev = self._idx(idx)
+        n = m if t is not None else (n or 0)
+        loss = torch.empty(1, device="cuda")
+        self._c(_abi.lib().dinr_forward(self._h, _ptr(t), n, on_dev, _ptr(loss)))
+        return loss
+
+    def backward_grad(self, dloss=None):
+        """Gradient of dloss * L for the minibatch of the last forward_loss
+        (dloss: a one-element CUDA float32 tensor, or None for 1)."""
+        grad = torch.empty(self.n_params, device="cuda")
+        d = None
+        if dloss is not None:
+            d = dloss.detach().reshape(1).to(device="cuda", dtype=torch.float32).contiguous()
+        self._c(_abi.lib().dinr_backward(self._h, _ptr(d), _ptr(grad)))
+        return grad
+
     def predict(self, idx):
         t, n, _ = self._idx(idx)
         out = torch.empty(n, device="cuda")
@@ -338,17 +357,17 @@ def phantom_project(geometry, phantom, idx=None):
 
 class DinrStep(torch.autograd.Function):
     """Loss of a DINR minibatch as an autograd function of a parameter
-    tensor: forward runs the library's forward model and loss, backward
-    returns the gradient computed by its hand-written adjoint kernels."""
+    tensor: forward runs the library's forward model and loss only;
+    backward launches its hand-written adjoint kernels for that minibatch
+    (on the activations the forward kept, or recomputing them when the
+    minibatch spans several workspace passes)."""
 
     @staticmethod
     def forward(ctx, params, model, idx):
         model.set_params(params.detach())
-        loss, grad = model.loss_grad(idx)
-        ctx.save_for_backward(grad)
-        return loss[0]
+        ctx.model = model
+        return model.forward_loss(idx)[0]
 
     @staticmethod
     def backward(ctx, g):
-        (grad,) = ctx.saved_tensors
-        return grad * g, None, None
+        return ctx.model.backward_grad(g), None, None
