@@ -12,9 +12,9 @@ Metric: training ray-samples per second (whole job over all ranks). A
 serving leg replays a seeded Poisson stream of mixed queries (time slices,
 sub-volumes, re-projections) against the query server of a cone-beam 6 x 256
 network and adds p50/p99 latency and outputs/s under "serving". An
-equal-error leg trains the BF16 and FP32 paths for 200 steps from the same
+equal-error leg trains the BF16 and FP32 paths for 1,000 steps from the same
 weights on the same minibatches and scores both reconstructions against the
-phantom ("equal_error").
+phantom every 250 steps ("equal_error").
 
 Our arm runs the library (default BF16 tensor-core path; the plain FP32 path
 is timed beside it). The reference arm (--impl reference) times the FP64 CPU
@@ -68,9 +68,11 @@ TRAFFIC = {"tc_fwd_chain": [dict(_CHAIN, bf16_workload=2,
                       "source": [_CSRC + f for f in ("tc_gemm.cu", "tc_gemm.cuh", "tc_ptx.cuh")],
                       "sha256_16": "de117760effc7867"}]}
 
-# Kernels bound by HBM bandwidth (their roofline is GB/s of algorithmic
-# bytes); the others are bound by the tensor pipe.
-HBM_BOUND = {"tc_dw", "dw_out", "encode"}
+# Kernels without tensor-core work of the method: their roofline is GB/s of
+# algorithmic bytes. Every other BF16 / FP8 kernel is measured against the
+# tensor pipe on the method's own FLOPs (the MLP GEMMs of the step); its HBM
+# figure (algorithmic bytes, stored activations included) is kept beside it.
+HBM_BOUND = {"dw_out", "encode"}
 
 
 def source_hash(paths):
@@ -98,17 +100,25 @@ def traffic_of(kernel, workload, samples, alg_bytes):
 
 def roofline_of(name, k, pk, src, prec, workload, samples_per_launch):
     """Roofline entry of one profiled kernel (k: launches, ms, flops, bytes
-    summed over its launches)."""
+    summed over its launches). Tensor-core kernels: achieved = the method's
+    FLOPs per launch / mean launch time, against the sustained BF16 peak
+    (the kernels run inside a long step) and, as frac_burst, the burst
+    peak; their algorithmic HBM bytes per launch over the same time under
+    "hbm"."""
     t = k["ms"] / k["launches"] / 1e3                       # seconds per launch
-    if name in HBM_BOUND:
-        ach = k["bytes"] / k["launches"] / t / 1e9
-        r = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-             "peak_source": f"hbm_gbs ({src})"}
+    hbm = {"achieved": k["bytes"] / k["launches"] / t / 1e9, "peak": pk["hbm_gbs"],
+           "unit": "GB/s", "peak_source": f"hbm_gbs ({src})"}
+    hbm["frac"] = hbm["achieved"] / hbm["peak"]
+    if name in HBM_BOUND or (prec in ("bf16", "fp8") and k["flops"] <= 0):
+        r = dict(hbm, bound="hbm")
     elif prec == "bf16" or prec == "fp8":
         ach = k["flops"] / k["launches"] / t / 1e12
-        peak = pk["bf16_tflops_sustained"] * (2 if prec == "fp8" else 1)
+        scale = 2 if prec == "fp8" else 1
+        peak = pk["bf16_tflops_sustained"] * scale
         r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-             "peak_source": ("2 x " if prec == "fp8" else "") + f"bf16_tflops_sustained ({src})"}
+             "peak_source": ("2 x " if prec == "fp8" else "") + f"bf16_tflops_sustained ({src})",
+             "frac_burst": ach / (pk["bf16_tflops"] * scale),
+             "peak_burst": pk["bf16_tflops"] * scale, "hbm": hbm}
     else:
         ach = k["flops"] / k["launches"] / t / 1e12
         r = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -362,10 +372,11 @@ def run_ours(args):
 
 
 def run_equal_error(args, w, proj, theta, rank):
-    """Reconstruction error after the same number of Adam steps on both paths
-    (same initial weights, same minibatch indices): relative L2 error and
-    PSNR of mu0 M against the phantom's attenuation on a 64^3 grid inside the
-    field of view, at 8 view times."""
+    """Reconstruction error along the same Adam trajectory length on both
+    paths (same initial weights, same minibatch indices): relative L2 error
+    and PSNR of mu0 M against the phantom's attenuation on a 64^3 grid
+    inside the field of view, at 8 view times, every `equal_error_every`
+    steps. Wall times exclude the scoring."""
     import torch
 
     from paper_2404_19075_b300 import Dinr
@@ -373,6 +384,7 @@ def run_equal_error(args, w, proj, theta, rank):
 
     g, net = w.geom, w.net
     B, steps = w.train.batch_rays, args.equal_error_steps
+    every = max(1, min(args.equal_error_every, steps))
     ph = wl.phantom(w)
     times = [(k + 0.5) / 8 for k in range(8)]
     mask = truth.fov_mask(64)
@@ -382,24 +394,33 @@ def run_equal_error(args, w, proj, theta, rank):
     for prec in ("bf16", "fp32"):
         m = Dinr(g, net, w.train, proj, prec=prec, init_params=theta,
                  sampler_seed=w.seeds["sampler"] + 1000 * rank)
-        losses = {}
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(1, steps + 1):
-            m.train_step(None, n=B, sync=False)
-            if k in (1, steps // 4, steps // 2, 3 * steps // 4, steps):
-                losses[k] = m.loss()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        sc = [truth.scores(m.query_grid(t, (-1, -1, -1), (1, 1, 1), (64, 64, 64)).cpu().numpy(),
-                           gt_t, mask) for t, gt_t in zip(times, gt)]
-        out[prec] = {"rel_l2": float(np.mean([x["rel_l2"] for x in sc])),
-                     "psnr_db": float(np.mean([x["psnr_db"] for x in sc])),
-                     "loss": losses, "wall_s": wall,
-                     "samples_per_s": steps * B * g.samples_per_ray / wall}
+        curve, wall = [], 0.0
+        for k0 in range(0, steps, every):
+            n = min(every, steps - k0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(n):
+                m.train_step(None, n=B, sync=False)
+            torch.cuda.synchronize()
+            wall += time.perf_counter() - t0
+            sc = [truth.scores(m.query_grid(t, (-1, -1, -1), (1, 1, 1), (64, 64, 64))
+                               .cpu().numpy(), gt_t, mask) for t, gt_t in zip(times, gt)]
+            curve.append({"step": k0 + n, "wall_s": wall, "loss": m.loss(),
+                          "rel_l2": float(np.mean([x["rel_l2"] for x in sc])),
+                          "psnr_db": float(np.mean([x["psnr_db"] for x in sc]))})
+        out[prec] = {"rel_l2": curve[-1]["rel_l2"], "psnr_db": curve[-1]["psnr_db"],
+                     "loss": curve[-1]["loss"], "wall_s": wall,
+                     "samples_per_s": steps * B * g.samples_per_ray / wall, "curve": curve}
         m.close()
-    out["bf16_over_fp32_rel_l2"] = out["bf16"]["rel_l2"] / out["fp32"]["rel_l2"]
+    fp32_final = out["fp32"]["rel_l2"]
+    out["bf16_over_fp32_rel_l2"] = out["bf16"]["rel_l2"] / fp32_final
     out["equal_error"] = out["bf16_over_fp32_rel_l2"] <= 1.02
+    # wall time each path takes to reach the FP32 path's final error (first
+    # scored step at or below 1.02 x that error)
+    for prec in ("bf16", "fp32"):
+        hit = next((c for c in out[prec]["curve"] if c["rel_l2"] <= 1.02 * fp32_final), None)
+        out[prec]["wall_s_to_fp32_final_error"] = hit["wall_s"] if hit else None
+        out[prec]["steps_to_fp32_final_error"] = hit["step"] if hit else None
     return out
 
 
@@ -431,6 +452,33 @@ def run_serving(args, rank):
     m.serve_policy("least_work")
     lw = serving.run(m, qs, time_limit=120.0)
     m.serve_policy("arrival")
+    # a rate the server can carry: 70 % of the samples per second of device
+    # time it served above, in requests of the stream's mean size; the same
+    # queries (kinds, sizes) arrive at that rate, under both policies, and
+    # the utilisation is the device time of the replay over its wall time
+    busy_s = sum(v["ms"] for k, v in prof.items() if not k.startswith("total_")) / 1e3
+    served = sum(serving.request_args(q)[3] for q in qs)
+    mean_smp = served / len(qs)
+    rate_sus = 0.7 * (served / busy_s) / mean_smp if busy_s > 0 else None
+    sus = None
+    if rate_sus:
+        qs2 = wl.query_stream(args.serve_queries, rate=rate_sus, seed=5000 + rank)
+        m.profile(True)
+        r2 = serving.run(m, qs2, time_limit=120.0)
+        m.profile(False)
+        p2 = m.profile_report()
+        busy2 = sum(v["ms"] for k, v in p2.items() if not k.startswith("total_")) / 1e3
+        m.serve_policy("least_work")
+        lw2 = serving.run(m, qs2, time_limit=120.0)
+        m.serve_policy("arrival")
+        sus = {"arrival_rate_per_s": rate_sus,
+               "offered_samples_per_s": rate_sus * mean_smp,
+               "capacity_samples_per_s": served / busy_s,
+               "utilisation": busy2 / r2["wall"],
+               "p50_ms": r2.get("p50_ms"), "p99_ms": r2.get("p99_ms"),
+               "completed": r2["completed"], "outputs_per_s": r2["outputs_per_s"],
+               "least_work_policy": {"p50_ms": lw2.get("p50_ms"), "p99_ms": lw2.get("p99_ms"),
+                                     "completed": lw2["completed"]}}
     # 4D export: 8 volumes of 256^3 streamed to pinned host memory
     ex_dims, ex_times = (256, 256, 256), [(k + 0.5) / 8 for k in range(8)]
     sums = []
@@ -463,6 +511,8 @@ def run_serving(args, rank):
                       "frac_of_bf16_sustained": tf / pk["bf16_tflops_sustained"] if tf else None,
                       "peak_source": f"bf16_tflops_sustained ({src})"},
             "gpu_launches": prof.get("total_launches", {}).get("launches"),
+            "utilisation": busy_s / res["wall"],
+            "sustainable_rate": sus,
             "export_4d": export,
             "clocks": ck.summary(),
             "config": "cone beam SOD 4 / SDD 8, MLP 6x256 ReLU, 10-octave encoding; "
@@ -504,6 +554,10 @@ def emit(args, w, results, ws):
                                                       "sub-pixel rays, samples per pixel vary"}
                                     if g.subpixels else {})}),
             "tflops_algorithmic": value * algorithmic_flops_per_sample(net) / 1e12,
+            **({"tflops_frac_sustained": value * algorithmic_flops_per_sample(net) / 1e12
+                / pk["bf16_tflops_sustained"],
+                "tflops_frac_burst": value * algorithmic_flops_per_sample(net) / 1e12
+                / pk["bf16_tflops"]} if args.prec == "bf16" else {}),
             "roofline": roof,
             "rooflines": major,
             "kernel_shares": {k: round(v["ms"] / total_ms, 4) for k, v in kern.items()},
@@ -544,8 +598,10 @@ def main():
                          "model)")
     ap.add_argument("--recompute", type=int, default=0,
                     help="activation recomputation of the unfused BF16 path (0, 1, -1 auto)")
-    ap.add_argument("--equal-error-steps", type=int, default=200,
+    ap.add_argument("--equal-error-steps", type=int, default=1000,
                     help="Adam steps of the BF16-vs-FP32 reconstruction comparison (0 skips it)")
+    ap.add_argument("--equal-error-every", type=int, default=250,
+                    help="steps between scorings of the reconstruction in that comparison")
     ap.add_argument("--serve-queries", type=int, default=200,
                     help="queries of the serving leg (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
