@@ -67,31 +67,12 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
-// Packed FP32 add of two pairs (one instruction on sm_100 and later).
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-  uint64_t d;
-  asm("add.rn.f32x2 %0, %1, %2;"
-      : "=l"(d)
-      : "l"(*reinterpret_cast<uint64_t *>(&a)), "l"(*reinterpret_cast<uint64_t *>(&b)));
-  return *reinterpret_cast<float2 *>(&d);
-}
-
-// Packed FP32 multiply and fused multiply-add of two pairs.
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;"
-      : "=l"(d)
-      : "l"(*reinterpret_cast<uint64_t *>(&a)), "l"(*reinterpret_cast<uint64_t *>(&b)));
-  return *reinterpret_cast<float2 *>(&d);
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;"
-      : "=l"(d)
-      : "l"(*reinterpret_cast<uint64_t *>(&a)), "l"(*reinterpret_cast<uint64_t *>(&b)),
-        "l"(*reinterpret_cast<uint64_t *>(&c)));
-  return *reinterpret_cast<float2 *>(&d);
-}
+// Packed FP32 add, multiply and fused multiply-add of two pairs (one
+// instruction each on sm_100 and later; the compiler's builtins, so that
+// the pairs stay in registers without packing moves).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // BF16 pair (lo, hi) of max(x, 0), rounded to nearest even.
 __device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
