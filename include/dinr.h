@@ -202,6 +202,20 @@ DINR_API dinr_status dinr_set_projections(dinr_ctx *ctx, const float *proj, int 
 DINR_API dinr_status dinr_train_step(dinr_ctx *ctx, const int64_t *ray_idx, int n,
                             int idx_on_device, float *loss_out);
 
+/* `steps` training steps of n rays each from the built-in sampler, as that
+ * many dinr_train_step(ctx, NULL, n, 0, ...) calls would run them (the
+ * same minibatches, learning rates of App. C and Adam bias corrections;
+ * bitwise the same parameters), replayed from a CUDA graph of one step:
+ * the first call for a given n captures the step on a private stream
+ * (the sampler and Adam read the step counter and a table of per-step
+ * learning rates and bias corrections from device memory), later calls
+ * replay it, ordered after and before the context stream's work by
+ * events. loss_out: host float, the last step's loss (the call then waits
+ * for it), or NULL (no wait). Steps of the App. A forward model (which
+ * read each pass's sample count back) and steps while profiling is on run
+ * as ordinary steps. Errors as dinr_train_step. */
+DINR_API dinr_status dinr_train_graph(dinr_ctx *ctx, int n, int steps, float *loss_out);
+
 /* Loss and gradient only (no Adam update), for a caller-owned optimiser or an
  * autograd wrapper. loss_dev: device float[1]; grad_dev: device
  * float[dinr_param_count]. Either may be NULL. Indices as in

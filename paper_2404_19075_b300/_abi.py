@@ -74,6 +74,7 @@ PROTOTYPES = {
     "dinr_train_step": (C.c_int, [vp, vp, C.c_int, C.c_int, C.POINTER(C.c_float)]),
     "dinr_loss_grad": (C.c_int, [vp, vp, C.c_int, C.c_int, vp, vp]),
     "dinr_forward": (C.c_int, [vp, vp, C.c_int, C.c_int, vp]),
+    "dinr_train_graph": (C.c_int, [vp, C.c_int, C.c_int, vp]),
     "dinr_backward": (C.c_int, [vp, vp, vp]),
     "dinr_predict": (C.c_int, [vp, vp, C.c_int, C.c_int, vp]),
     "dinr_project": (C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, vp]),

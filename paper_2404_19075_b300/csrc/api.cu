@@ -316,6 +316,10 @@ void dinr_destroy(dinr_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
   dinr_serve_release(c);
+  if (c->gexec) cudaGraphExecDestroy((cudaGraphExec_t)c->gexec);
+  for (cudaEvent_t e : c->gev)
+    if (e) cudaEventDestroy(e);
+  if (c->gst) cudaStreamDestroy(c->gst);
   destroy_backend(c);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   for (void *p : c->allocs) cudaFree(p);
@@ -449,6 +453,130 @@ dinr_status dinr_train_step(dinr_ctx *c, const int64_t *idx, int n, int on_devic
   if (loss_out) {
     CK(cudaMemcpyAsync(loss_out, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost, c->st));
     s = backend_poll(c);
+    if (s != DINR_OK) return s;
+    if (!std::isfinite(*loss_out))
+      return (dinr_status)dinr_fail(c, DINR_ERR_NONFINITE, "loss is not finite");
+  }
+  return DINR_OK;
+}
+
+// The learning rate and Adam bias corrections of step `step` (0-based; Adam
+// step t = step + 1), as dinr_train_step computes them.
+static void step_scalars(const dinr_ctx *c, long long step, int n, float *out) {
+  const long long spe = (c->n_proj + n - 1) / n;
+  const long long t = step + 1;
+  out[0] = (float)(c->lr * std::pow(c->decay, (double)(step / spe)));
+  out[1] = (float)(1.0 / (1.0 - std::pow(c->b1, (double)t)));
+  out[2] = (float)(1.0 / (1.0 - std::pow(c->b2, (double)t)));
+}
+
+// Captures one training step of n sampled rays on the private stream: the
+// sampler reading the device step counter, loss and gradient, Adam from
+// the table, the parameter copies, the counter's increment.
+static dinr_status capture_step(dinr_ctx *c, int n) {
+  if (!c->gst) {
+    CK(cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : c->gev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  if (c->gexec) {
+    cudaGraphExecDestroy((cudaGraphExec_t)c->gexec);
+    c->gexec = nullptr;
+  }
+  cudaStream_t user = c->st;
+  c->st = c->gst;
+  cudaError_t e = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeRelaxed);
+  dinr_status s = DINR_OK;
+  if (e == cudaSuccess) {
+    launch_sample_indices_dev(c->n_proj, n, c->d_step, c->sampler_seed, c->d_idx, c->st);
+    ++c->launches;
+    s = run_loss_grad(c, n);
+    if (s == DINR_OK) {
+      launch_adam_tab(c->d_params, c->d_m, c->d_v, c->d_grad, c->P, (float)c->b1, (float)c->b2,
+                      (float)c->eps, c->d_sched, c->d_step, c->d_step0, c->st);
+      ++c->launches;
+      s = after_param_update(c);
+    }
+    if (s == DINR_OK) {
+      launch_step_inc(c->d_step, c->st);
+      ++c->launches;
+    }
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c->gst, &g) : e;
+  c->st = user;
+  if (s != DINR_OK || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (s != DINR_OK) return s;
+    return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "step capture: %s", cudaGetErrorString(e2));
+  }
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  long long kernels = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess)
+    return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "step graph: %s", cudaGetErrorString(e));
+  c->gexec = ex;
+  c->g_rays = n;
+  c->g_kernels = kernels;
+  return DINR_OK;
+}
+
+dinr_status dinr_train_graph(dinr_ctx *c, int n, int steps, float *loss_out) {
+  LIVE(c);
+  if (n < 1 || n > c->batch_rays || steps < 1)
+    return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "n = %d outside [1, %d] or steps = %d < 1", n,
+                                  c->batch_rays, steps);
+  if (c->geo.D > 0 || c->prof) {
+    // App. A steps read each pass's sample count back to the host, and
+    // profiling times every launch: both run as ordinary steps
+    for (int k = 0; k < steps; ++k) {
+      dinr_status s = dinr_train_step(c, nullptr, n, 0, k + 1 == steps ? loss_out : nullptr);
+      if (s != DINR_OK) return s;
+    }
+    return DINR_OK;
+  }
+  c->fwd_n = 0;  // the graph restages the minibatch indices
+  c->fwd_kept = false;
+  bool ok = true;
+  if (!c->d_step) {
+    c->d_step = (long long *)dev_alloc(c, 2 * sizeof(long long), &ok);
+    if (ok) c->d_step0 = c->d_step + 1;
+  }
+  if (ok && steps > c->sched_cap) {
+    const int cap = steps > 1024 ? steps : 1024;
+    c->d_sched = (float *)dev_alloc(c, sizeof(float) * 3 * (size_t)cap, &ok);
+    if (ok) c->sched_cap = cap;
+  }
+  if (!ok) return (dinr_status)dinr_fail(c, DINR_ERR_OOM, "step graph state: out of memory");
+  std::vector<float> tab(3 * (size_t)steps);
+  for (int k = 0; k < steps; ++k) step_scalars(c, c->step + k, n, &tab[3 * (size_t)k]);
+  const long long s0[2] = {c->step, c->step};
+  // pageable host sources: each copy has taken its bytes when the call returns
+  CK(cudaMemcpyAsync(c->d_sched, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice,
+                     c->st));
+  CK(cudaMemcpyAsync(c->d_step, s0, sizeof(s0), cudaMemcpyHostToDevice, c->st));
+  if (!c->gexec || c->g_rays != n) {
+    dinr_status s = capture_step(c, n);
+    if (s != DINR_OK) return s;
+  }
+  CK(cudaEventRecord(c->gev[0], c->st));
+  CK(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
+  for (int k = 0; k < steps; ++k) CK(cudaGraphLaunch((cudaGraphExec_t)c->gexec, c->gst));
+  CK(cudaEventRecord(c->gev[1], c->gst));
+  CK(cudaStreamWaitEvent(c->st, c->gev[1], 0));
+  c->step += steps;
+  c->launches += c->g_kernels * steps;
+  if (loss_out) {
+    CK(cudaMemcpyAsync(loss_out, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    dinr_status s = backend_poll(c);
     if (s != DINR_OK) return s;
     if (!std::isfinite(*loss_out))
       return (dinr_status)dinr_fail(c, DINR_ERR_NONFINITE, "loss is not finite");

@@ -60,6 +60,19 @@ struct dinr_ctx {
   float *part = nullptr;
   long long part_floats = 0;
 
+  // Graph-replayed training steps (dinr_train_graph): one step captured
+  // once per minibatch size and replayed on a private stream; the step
+  // counter and a table of per-step learning rates and bias corrections
+  // live in device memory while it runs.
+  long long *d_step = nullptr, *d_step0 = nullptr;
+  float *d_sched = nullptr;       // [sched_cap][3]
+  int sched_cap = 0;
+  void *gexec = nullptr;          // cudaGraphExec_t of one step
+  int g_rays = 0;                 // minibatch size it was captured for
+  long long g_kernels = 0;        // kernel nodes of the graph
+  cudaStream_t gst = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+
   // BF16 (tensor-core) backend state, owned by the tensor-core pipeline.
   void *tc = nullptr;
   // query server state (serve.cu)

@@ -139,6 +139,16 @@ void launch_loss_sum(const float *sq, long long n, float inv_B, float *loss, boo
                      cudaStream_t st);
 
 // Adam (Kingma & Ba), FP32 master weights.
+// The sampler with its step read from device memory.
+void launch_sample_indices_dev(long long n_proj, int B, const long long *step, uint64_t seed,
+                               long long *out, cudaStream_t st);
+// Adam with the learning rate and bias corrections of step *step from
+// tab[3 (*step - *step0) ..] (lr, 1 / (1 - beta1^t), 1 / (1 - beta2^t)).
+void launch_adam_tab(float *theta, float *m, float *v, const float *g, long long P, float beta1,
+                     float beta2, float eps, const float *tab, const long long *step,
+                     const long long *step0, cudaStream_t st);
+// *step += 1 on the device.
+void launch_step_inc(long long *step, cudaStream_t st);
 // out = g * (*scale) over P floats (scale: device float[1]).
 void launch_scale_by(const float *g, long long P, const float *scale, float *out,
                      cudaStream_t st);

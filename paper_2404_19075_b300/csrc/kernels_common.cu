@@ -20,10 +20,8 @@ __device__ __forceinline__ uint64_t feistel(uint64_t x, const uint64_t *key, int
   return (L << h) | R;
 }
 
-__global__ void k_sample(long long n, int B, long long step, uint64_t seed, int h,
-                         long long *out) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+__device__ __forceinline__ long long sample_index(long long n, int B, long long step,
+                                                  uint64_t seed, int h, int b) {
   long long spe = (n + B - 1) / B;
   long long e = step / spe, j = step - e * spe;
   uint64_t key[4];
@@ -33,15 +31,36 @@ __global__ void k_sample(long long n, int B, long long step, uint64_t seed, int 
   uint64_t y = feistel(x, key, h);
   // Cycle walking ends: x < n lies on the cycle of a bijection.
   while (y >= (uint64_t)n) y = feistel(y, key, h);
-  out[b] = (long long)y;
+  return (long long)y;
+}
+
+__global__ void k_sample(long long n, int B, long long step, uint64_t seed, int h,
+                         long long *out) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) out[b] = sample_index(n, B, step, seed, h, b);
+}
+
+// The same with the step read from device memory (graph-replayed steps).
+__global__ void k_sample_dev(long long n, int B, const long long *step, uint64_t seed, int h,
+                             long long *out) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) out[b] = sample_index(n, B, *step, seed, h, b);
+}
+
+static int sampler_half_bits(long long n) {
+  int bits = 2;
+  while ((1LL << bits) < n) ++bits;
+  return (bits + 1) / 2;
 }
 
 void launch_sample_indices(long long n, int B, long long step, uint64_t seed, long long *out,
                            cudaStream_t st) {
-  int bits = 2;
-  while ((1LL << bits) < n) ++bits;
-  int h = (bits + 1) / 2;
-  k_sample<<<ceil_div(B, 256), 256, 0, st>>>(n, B, step, seed, h, out);
+  k_sample<<<ceil_div(B, 256), 256, 0, st>>>(n, B, step, seed, sampler_half_bits(n), out);
+}
+
+void launch_sample_indices_dev(long long n, int B, const long long *step, uint64_t seed,
+                               long long *out, cudaStream_t st) {
+  k_sample_dev<<<ceil_div(B, 256), 256, 0, st>>>(n, B, step, seed, sampler_half_bits(n), out);
 }
 
 __global__ void k_check_indices(long long *idx, int n, long long n_proj, int *bad) {
@@ -515,6 +534,36 @@ void launch_adam(float *theta, float *m, float *v, const float *g, long long P, 
   k_adam<<<ceil_div(P, 256), 256, 0, st>>>(theta, m, v, g, P, lr, beta1, beta2, eps, bc1, bc2);
 }
 
+
+// Adam of a graph-replayed step: the same update as k_adam with the step's
+// learning rate and bias corrections read from a host-filled table, entry
+// (*step - *step0).
+__global__ void k_adam_tab(float *theta, float *m, float *v, const float *g, long long P,
+                           float beta1, float beta2, float eps, const float *tab,
+                           const long long *step, const long long *step0) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const long long k = *step - *step0;
+  const float lr = tab[3 * k], bc1 = tab[3 * k + 1], bc2 = tab[3 * k + 2];
+  float gi = g[i];
+  float mi = beta1 * m[i] + (1.0f - beta1) * gi;
+  float vi = beta2 * v[i] + (1.0f - beta2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi * bc1) / (sqrtf(vi * bc2) + eps);
+}
+void launch_adam_tab(float *theta, float *m, float *v, const float *g, long long P, float beta1,
+                     float beta2, float eps, const float *tab, const long long *step,
+                     const long long *step0, cudaStream_t st) {
+  k_adam_tab<<<ceil_div(P, 256), 256, 0, st>>>(theta, m, v, g, P, beta1, beta2, eps, tab, step,
+                                               step0);
+}
+
+// *step += 1 (the end of a graph-replayed step).
+__global__ void k_step_inc(long long *step) {
+  if (threadIdx.x == 0) *step += 1;
+}
+void launch_step_inc(long long *step, cudaStream_t st) { k_step_inc<<<1, 32, 0, st>>>(step); }
 
 // out[i] = g[i] * (*scale): the gradient of (scale x L) from that of L (the
 // upstream factor an autograd backward passes in).

@@ -141,6 +141,14 @@ class Dinr:
                                            C.byref(out) if sync else None))
         return out.value if sync else None
 
+    def train_graph(self, n, steps, sync=True):
+        """`steps` steps of n sampled rays replayed from a CUDA graph of one
+        step (bitwise the same as that many train_step(None, n) calls);
+        returns the last step's loss when sync, else None."""
+        out = C.c_float()
+        self._c(_abi.lib().dinr_train_graph(self._h, n, steps, C.byref(out) if sync else None))
+        return out.value if sync else None
+
     def train_step_host(self, idx_host, sync=True):
         """One step with indices in host memory (an int64 numpy array or a
         CPU tensor, ideally pinned); the library copies them itself."""

@@ -55,6 +55,39 @@ def test_forward_then_backward_equals_loss_grad(prec, chunk):
         m.close()
 
 
+@pytest.mark.parametrize("case", ["subpixel", "wide", "fp8"])
+def test_split_on_other_paths(case):
+    """The same split on the App. A forward model (sub-pixel rays through
+    the fused chains, two passes), the wide unfused network (512-wide
+    layers) and the FP8 forward variant: bitwise the combined call."""
+    require_gpu()
+    from dataclasses import replace
+    if case == "subpixel":
+        w = wl.workload(9)
+        n, prec, chunk, net = 96, "bf16", 48, wl.workload(9).net
+    elif case == "wide":
+        w = wl.workload(1)
+        net = replace(w.net, width=512, hidden_layers=2, out_act="identity")
+        n, prec, chunk = 64, "bf16", 0
+    else:
+        w = wl.workload(3)
+        n, prec, chunk, net = 64, "fp8", 0, wl.workload(3).net
+    idx = wl.ray_subset(w.geom.n_proj, n, 64)
+    params = wl.he_init(net, w.seeds["weights"])
+    # two fresh contexts (the FP8 delayed scales move after every step)
+    m1, _, proj = make_model(w, prec, idx=idx, net=net, batch=n, chunk=chunk, params=params)
+    m2, _, _ = make_model(w, prec, proj=proj, net=net, batch=n, chunk=chunk, params=params)
+    try:
+        loss_ref, grad_ref = m1.loss_grad(idx)
+        loss = m2.forward_loss(idx)
+        grad = m2.backward_grad()
+        assert torch.equal(loss, loss_ref)
+        assert torch.equal(grad, grad_ref)
+    finally:
+        m1.close()
+        m2.close()
+
+
 def test_autograd_function_bf16():
     require_gpu()
     from paper_2404_19075_b300 import DinrStep
