@@ -316,6 +316,7 @@ void dinr_destroy(dinr_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
   dinr_serve_release(c);
+  if (c->gst) cudaStreamSynchronize(c->gst);  // replays in flight finish first
   if (c->gexec) cudaGraphExecDestroy((cudaGraphExec_t)c->gexec);
   for (cudaEvent_t e : c->gev)
     if (e) cudaEventDestroy(e);
