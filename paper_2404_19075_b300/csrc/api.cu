@@ -484,6 +484,7 @@ static dinr_status capture_step(dinr_ctx *c, int n) {
     c->gexec = nullptr;
   }
   cudaStream_t user = c->st;
+  const long long launches = c->launches;  // captured launches run only when replayed
   c->st = c->gst;
   cudaError_t e = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeRelaxed);
   dinr_status s = DINR_OK;
@@ -505,22 +506,26 @@ static dinr_status capture_step(dinr_ctx *c, int n) {
   cudaGraph_t g = nullptr;
   cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c->gst, &g) : e;
   c->st = user;
+  c->launches = launches;
   if (s != DINR_OK || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     if (s != DINR_OK) return s;
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "step capture: %s", cudaGetErrorString(e2));
   }
   size_t nn = 0;
-  CK(cudaGraphGetNodes(g, nullptr, &nn));
-  std::vector<cudaGraphNode_t> nodes(nn);
-  CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  std::vector<cudaGraphNode_t> nodes;
+  e = cudaGraphGetNodes(g, nullptr, &nn);
+  if (e == cudaSuccess) {
+    nodes.resize(nn);
+    e = cudaGraphGetNodes(g, nodes.data(), &nn);
+  }
   long long kernels = 0;
   for (cudaGraphNode_t nd : nodes) {
     cudaGraphNodeType ty;
     if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
   }
   cudaGraphExec_t ex = nullptr;
-  e = cudaGraphInstantiate(&ex, g, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess)
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "step graph: %s", cudaGetErrorString(e));
