@@ -1,11 +1,12 @@
 // Fused forward and backward chains (see tc_chain.cuh).
 //
-// One persistent CTA per SM, 320 threads:
+// One persistent CTA per SM, 320 threads (576 in the ReLU backward):
 //   warp 0      one thread streams the weight K-chunks of every layer by TMA
 //               into an S-stage ring (each chunk once per tile)
 //   warp 1      TMEM owner; one thread issues tcgen05.mma (M = 128, N = W,
 //               K = 16) for every layer of two 128-sample tiles in turn
-//   warps 2..9  two per TMEM lane quadrant: build the layer-0 input of a
+//   warps 2..9  two per TMEM lane quadrant (the ReLU backward: warps 2..17,
+//               four per quadrant, one 64-column chunk each): build the layer-0 input of a
 //               tile in shared memory (ray generation + Fourier features,
 //               Sec. III, App. A, App. B), then after each layer read the
 //               accumulator, add the bias, apply ReLU, write the BF16
@@ -25,8 +26,15 @@ using namespace tc;
 
 namespace {
 
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
+// Epilogue warps per TMEM lane quadrant ("parts"; part p owns the 64-column
+// chunks jc with jc % parts == p): two, or four in the ReLU backward chain,
+// whose epilogue is short enough for the 96 registers a thread of 18 warps
+// gets (the forward's and the Swish epilogues need more).
+template <bool kBwd, int kAct>
+constexpr int parts_of() { return (kBwd && kAct == kActRelu) ? 4 : 2; }
+template <bool kBwd, int kAct>
+constexpr int threads_of() { return 64 + 128 * parts_of<kBwd, kAct>(); }
+constexpr int kEpiWarps = 8;  // forward chains (the dot-product exchange)
 constexpr int kChunkBytes = 128 * 128;  // 128 rows x 64 BF16 (one K-chunk, 128B swizzle)
 constexpr int kSmemLimit = 232448;
 
@@ -602,13 +610,14 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
 
 
 // Store this warp's chunks of the tile buffer through maps.h[L].
+template <int kP>
 __device__ __forceinline__ void store_chunks(const ChainMaps &maps, const ChainArgs &p,
                                              uint8_t *A, int L, long long tile, int q, int half,
                                              int lane) {
   fence_async_smem();
   __syncwarp();
   if (lane == 0 && p.store_h && tile * 128 + q * 32 < p.ns) {
-    for (int jc = half; jc < p.W / 64; jc += 2)
+    for (int jc = half; jc < p.W / 64; jc += kP)
       tma_store_2d(&maps.h[L], A + (size_t)jc * kChunkBytes + q * 32 * 128, 64 * jc,
                    (int)(tile * 128 + q * 32));
     bulk_commit();
@@ -617,7 +626,7 @@ __device__ __forceinline__ void store_chunks(const ChainMaps &maps, const ChainA
 
 // delta_{H-1}[s][c] = dz[s] * w_out[c] * act'(.) into the tile buffer: the
 // ReLU bit of h_{H-1}, or the stored Swish derivative.
-template <int kAct>
+template <int kAct, int kP>
 __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t *A,
                              long long tile, int q, int half, int lane) {
   const int r_in = q * 32 + lane;
@@ -625,7 +634,7 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
   const bool live = row < p.ns;
   const float dzr = live ? p.dz[row] : 0.0f;
   if constexpr (kAct == kActSwish) {
-    for (int jc = half; jc < p.W / 64; jc += 2) {
+    for (int jc = half; jc < p.W / 64; jc += kP) {
       uint8_t *chunk = A + (size_t)jc * kChunkBytes;
       uint4 gq[8];  // the chunk's derivatives, all loads in flight together
 #pragma unroll
@@ -644,10 +653,10 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
         *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
-    store_chunks(maps, p, A, p.H - 1, tile, q, half, lane);
+    store_chunks<kP>(maps, p, A, p.H - 1, tile, q, half, lane);
     return;
   }
-  for (int jc = half; jc < p.W / 64; jc += 2) {
+  for (int jc = half; jc < p.W / 64; jc += kP) {
     const uint2 mb = live ? ld_stream2(mask_unit(p, p.H - 1, row, jc)) : make_uint2(0u, 0u);
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
 #pragma unroll
@@ -663,7 +672,7 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
-  store_chunks(maps, p, A, p.H - 1, tile, q, half, lane);
+  store_chunks<kP>(maps, p, A, p.H - 1, tile, q, half, lane);
 }
 
 // Swish: delta_{L-1} = acc * g_{L-1} with the derivative the forward stored;
@@ -715,12 +724,33 @@ __device__ bool bwd_epilogue_swish(const ChainMaps &maps, const ChainArgs &p, co
       for (int c16 = 0; c16 < 8; ++c16) gq[c16] = gn[c16];
     }
   }
-  store_chunks(maps, p, A, L - 1, tile, q, half, lane);
+  store_chunks<2>(maps, p, A, L - 1, tile, q, half, lane);
   return true;
 }
 
+// delta = acc * [h > 0] for the 32 columns c0 .. c0 + 31 whose accumulators
+// are in r, with the group's mask word m (pair k at bits 15 - k and
+// 31 - k), in BF16 into the tile buffer.
+__device__ __forceinline__ void bwd_relu_group(uint8_t *A, int c0, const uint32_t (&r)[32],
+                                               uint32_t m, int r_in) {
+  uint32_t ms[8];  // the mask word shifted by 0..7 (pairs k and k + 8 share one)
+#pragma unroll
+  for (int j = 0; j < 8; ++j) ms[j] = m << j;
+  uint32_t w[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    w[k] = pack2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1])) &
+           pair_mask_sh(ms[k & 7], k);
+  const int jc = c0 >> 6, hh = (c0 >> 5) & 1;
+  uint8_t *chunk = A + (size_t)jc * kChunkBytes;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    *reinterpret_cast<uint4 *>(chunk + swz(r_in, 4 * hh + u)) =
+        make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+}
+
 // After the input-gradient GEMM through layer L: delta_{L-1} = acc * [h_{L-1} > 0].
-template <int kAct>
+template <int kAct, int kP>
 __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Smem &s, int slot,
                              uint32_t tcol, int L, long long tile, int q, int half, int lane,
                              uint32_t tfull_phase) {
@@ -732,14 +762,29 @@ __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Sm
 
   uint2 mb[2] = {make_uint2(0u, 0u), make_uint2(0u, 0u)};
   if (live)  // before the wait: the ReLU bits of this warp's (at most two) chunks
-    for (int k = 0; k < 2 && half + 2 * k < p.W / 64; ++k)
-      mb[k] = ld_stream2(mask_unit(p, L - 1, row, half + 2 * k));
+    for (int k = 0; k < 2 && half + kP * k < p.W / 64; ++k)
+      mb[k] = ld_stream2(mask_unit(p, L - 1, row, half + kP * k));
   if (!warp_wait(&s.tfull[slot], tfull_phase & 1, p.err, 18)) return false;
   tc_fence_after();
   if (lane == 0) bulk_wait_read();
   __syncwarp();
   const uint32_t trow = tcol + ((uint32_t)(q * 32) << 16);
   uint8_t *A = s.A[slot];
+  if constexpr (kP > 2) {
+    // one chunk per warp, 32 columns at a time (the register budget of 18 warps)
+    for (int k = 0, jc = half; jc < p.W / 64; ++k, jc += kP) {
+      const uint2 m2 = k == 0 ? mb[0] : mb[1];
+      uint32_t r[32];
+      tmem_ld32_issue(trow + 64 * jc, r);
+      tmem_wait_ld32(r);
+      bwd_relu_group(A, 64 * jc, r, m2.x, r_in);
+      tmem_ld32_issue(trow + 64 * jc + 32, r);
+      tmem_wait_ld32(r);
+      bwd_relu_group(A, 64 * jc + 32, r, m2.y, r_in);
+    }
+    store_chunks<kP>(maps, p, A, L - 1, tile, q, half, lane);
+    return true;
+  }
   for (int k = 0, jc = half; jc < p.W / 64; ++k, jc += 2) {
     float v[64];
     tmem_ld64(trow + 64 * jc, v);
@@ -764,7 +809,7 @@ __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Sm
       *reinterpret_cast<uint4 *>(chunk + swz(r_in, c16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
-  store_chunks(maps, p, A, L - 1, tile, q, half, lane);
+  store_chunks<2>(maps, p, A, L - 1, tile, q, half, lane);
   return true;
 }
 
@@ -773,8 +818,9 @@ __device__ bool bwd_epilogue(const ChainMaps &maps, const ChainArgs &p, const Sm
 template <int F, bool kBwd, int kAct>
 __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
                                uint32_t tbase) {
+  constexpr int kP = parts_of<kBwd, kAct>();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int q = warp & 3, half = (warp - 2) / 4;
+  const int q = warp & 3, half = (warp - 2) / 4;  // half: this warp's part (0 .. kP - 1)
   const int np = n_pairs(p);
   const int ns = n_steps<kBwd>(p);
   uint32_t waits[2] = {0, 0}, dots[2] = {0, 0};
@@ -784,7 +830,7 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
   };
   auto start_tile = [&](int slot, long long tile) {
     if (kBwd)
-      bwd_prologue<kAct>(maps, p, s.A[slot], tile, q, half, lane);
+      bwd_prologue<kAct, kP>(maps, p, s.A[slot], tile, q, half, lane);
     else
       encode_tile<F>(maps, p, s.A[slot], tile, q, half, lane);
   };
@@ -800,8 +846,8 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
         const bool last = i == ns - 1;
         const uint32_t tcol = tbase + (uint32_t)(slot * p.W);
         if (kBwd) {
-          if (!bwd_epilogue<kAct>(maps, p, s, slot, tcol, step_layer<true>(p, i), tile, q, half,
-                                  lane, waits[slot]++))
+          if (!bwd_epilogue<kAct, kP>(maps, p, s, slot, tcol, step_layer<true>(p, i), tile, q,
+                                      half, lane, waits[slot]++))
             return;
         } else {
           if (!warp_wait(&s.tfull[slot], waits[slot]++ & 1, p.err, 17)) return;
@@ -823,7 +869,7 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
 }
 
 template <int F, bool kBwd, int kAct>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_of<kBwd, kAct>(), 1)
     k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -838,7 +884,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&s.empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&s.aready[i], kEpiWarps);
+      mbar_init(&s.aready[i], 4 * parts_of<kBwd, kAct>());
       mbar_init(&s.tfull[i], 1);
       mbar_init(&s.dotbar[i], kEpiWarps / 2);
     }
@@ -889,7 +935,7 @@ static int launch_fa(const ChainMaps &maps, const ChainArgs &a, int num_sms, cud
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   int grid = a.m_tiles < num_sms ? a.m_tiles : num_sms;
-  k_chain<F, kBwd, kAct><<<grid, kThreads, smem, st>>>(maps, a);
+  k_chain<F, kBwd, kAct><<<grid, threads_of<kBwd, kAct>(), smem, st>>>(maps, a);
   return (int)cudaGetLastError();
 }
 
