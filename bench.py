@@ -62,10 +62,11 @@ TRAFFIC = {"tc_fwd_chain": [dict(_CHAIN, bf16_workload=2,
                                  bytes_per_sample=(7.584768e6 + 3.011472e9) / 1048576)],
            "tc_bwd_chain": [dict(_CHAIN, bf16_workload=2,
                                  bytes_per_sample=(177.04192e6 + 2.625203e9) / 1048576)],
-           "tc_dw": [{"ratio_to_algorithmic": (1.075507e9 + 6.65728e6) / (2 * 1048576 * 256 * 2),
+           "tc_dw": [{"ratio_to_algorithmic": (1.074768e9 + 5.895424e6) / (2 * 1048576 * 256 * 2),
                       "bf16_workload": 2,
-                      "source": [_CSRC + f for f in ("tc_gemm.cu", "tc_gemm.cuh", "tc_ptx.cuh")],
-                      "sha256_16": "de117760effc7867"}]}
+                      "source": [_CSRC + f for f in ("tc_gemm.cu", "tc_gemm.cuh", "tc_ptx.cuh",
+                                                     "tc_pair.cuh")],
+                      "sha256_16": "448890cd40cb992b"}]}
 
 # Kernels without tensor-core work of the method: their roofline is GB/s of
 # algorithmic bytes. Every other BF16 / FP8 kernel is measured against the

@@ -9,7 +9,20 @@
 // Accumulators are double-buffered in TMEM when they fit, so the epilogue
 // of one tile overlaps the MMAs of the next. Every mbarrier wait is bounded
 // in time; a timeout sets *err and the roles wind down without hanging.
+//
+// Pair mode (k_tc_gemm_pair, clusters of two CTAs on two SMs; the weight
+// gradients dW = delta^T h with MN-major operands): a tile is 256 rows
+// (output neurons) x N; the even CTA's MMA thread issues
+// tcgen05.mma.cta_group::2 with M = 256, each CTA loading its own 128 rows
+// of A (delta columns) and half of the N columns of B (h), and each CTA's
+// epilogue reads its own 128 rows of D from its TMEM. Per SM this halves the
+// B operand streamed through TMA and read by the tensor core, and the h
+// block of a K step is fetched once per pair instead of once per CTA. Both
+// CTAs' loads of a stage count on the even CTA's stage barrier; MMA
+// completions are multicast to both CTAs' barriers; the odd CTA's epilogue
+// releases an accumulator to the even CTA remotely.
 #include "tc_gemm.cuh"
+#include "tc_pair.cuh"
 #include "tc_ptx.cuh"
 
 #include <cudaTypedefs.h>
@@ -60,11 +73,28 @@ __device__ __forceinline__ int acc_stride(const TcGemmArgs &p) {
 
 __device__ __forceinline__ int n_tn(const TcGemmArgs &p) { return p.n_tn > 1 ? p.n_tn : 1; }
 
-// Tile t -> M tile, N tile, K split and the K range of the split.
+// M units a tile index runs over: 128-row tiles, or pairs of them.
+__device__ __forceinline__ int m_units(const TcGemmArgs &p) {
+  return p.pair ? (p.m_tiles + 1) / 2 : p.m_tiles;
+}
+__device__ __forceinline__ int n_tiles_of(const TcGemmArgs &p) {
+  return m_units(p) * (p.n_tn > 1 ? p.n_tn : 1) * p.splits;
+}
+// This CTA's first tile and tile stride (a pair shares its tiles).
+__device__ __forceinline__ int first_tile(const TcGemmArgs &p) {
+  return p.pair ? (int)blockIdx.x / 2 : (int)blockIdx.x;
+}
+__device__ __forceinline__ int tile_stride(const TcGemmArgs &p) {
+  return p.pair ? (int)gridDim.x / 2 : (int)gridDim.x;
+}
+
+// Tile t -> M tile (of this CTA of a pair: rank), N tile, K split and the
+// K range of the split.
 __device__ __forceinline__ void tile_range(const TcGemmArgs &p, int t, int &mt, int &nt, int &sp,
-                                           long long &k0, int &nk) {
-  mt = t % p.m_tiles;
-  const int rest = t / p.m_tiles;
+                                           long long &k0, int &nk, int rank = 0) {
+  const int mu = m_units(p);
+  mt = p.pair ? 2 * (t % mu) + rank : t % mu;
+  const int rest = t / mu;
   nt = rest % n_tn(p);
   sp = rest / n_tn(p);
   k0 = (long long)sp * p.k_per_split;
@@ -86,27 +116,43 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
+template <bool kPair>
 __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcGemmArgs &p,
                          const Smem &s) {
   prefetch_tmap(ta);
   prefetch_tmap(tb);
   const int S = p.stages;
-  const uint32_t nb_mn = (uint32_t)((p.N + 63) / 64);
+  const uint32_t nb_mn = (uint32_t)(((kPair ? p.N / 2 : p.N) + 63) / 64);
   const uint32_t tx = (uint32_t)p.a_bytes + (uint32_t)p.b_bytes;
   uint32_t it = 0;
-  const int n_tiles = p.m_tiles * n_tn(p) * p.splits;
-  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  const int rank = kPair ? (int)cluster_ctarank() : 0;
+  const int n_tiles = n_tiles_of(p);
+  for (int t = first_tile(p); t < n_tiles; t += tile_stride(p)) {
     int mt, nt, sp, nk;
     long long k0;
-    tile_range(p, t, mt, nt, sp, k0, nk);
-    const int n0 = nt * p.N;
+    tile_range(p, t, mt, nt, sp, k0, nk, rank);
+    // a pair's B tile: this CTA's half of the N rows
+    const int n0 = nt * p.N + (kPair ? rank * (p.N / 2) : 0);
     for (int kb = 0; kb < nk; ++kb, ++it) {
       uint32_t st = it % S, rd = it / S;
       if (!mbar_wait(&s.empty[st], (rd & 1) ^ 1, p.err, 1)) return;
-      mbar_expect_tx(&s.full[st], tx);
       int kx = (int)(k0 + (long long)kb * (p.fp8 ? 2 * BK : BK));
       uint8_t *da = s.a + (size_t)st * p.a_bytes;
       uint8_t *db = s.b + (size_t)st * p.b_bytes;
+      if constexpr (kPair) {
+        // both CTAs' loads count on the even CTA's barrier, which expects
+        // the bytes of both (its MMA thread reads both halves)
+        if (rank == 0) mbar_expect_tx(&s.full[st], 2 * tx);
+        const uint32_t bar = mapa_shared(smem_u32(&s.full[st]), 0);
+        // (pair mode: MN-major A and B) this CTA's 128 columns of delta and
+        // its half of the N columns of h
+        tma_load_2d_pair(ta, bar, da, mt * BM, kx);
+        tma_load_2d_pair(ta, bar, da + 8192, mt * BM + 64, kx);
+        for (uint32_t j = 0; j < nb_mn; ++j)
+          tma_load_2d_pair(tb, bar, db + 8192 * j, n0 + 64 * (int)j, kx);
+        continue;
+      }
+      mbar_expect_tx(&s.full[st], tx);
       if (!p.a_mn) {
         tma_load_2d(ta, &s.full[st], da, kx, mt * BM);
       } else {
@@ -121,7 +167,11 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
       }
     }
   }
-  // Before the CTA can exit, every load issued must have landed.
+  // Before the CTA can exit, every load issued must have landed (a pair's
+  // loads are counted on the even CTA's barriers: the odd CTA's landed
+  // before the even CTA's MMAs read them, and the final cluster barrier
+  // keeps the odd CTA alive until then).
+  if (kPair && rank != 0) return;
   uint32_t n = it < (uint32_t)S ? it : (uint32_t)S;
   for (uint32_t q = it - n; q < it; ++q) {
     uint32_t st = q % S, rd = q / S;
@@ -129,17 +179,20 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
   }
 }
 
+template <bool kPair>
 __device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
   const int S = p.stages;
   const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
-  const uint32_t idesc = p.fp8 ? idesc_e4m3(BM, p.N) : idesc_bf16(BM, p.N, p.a_mn, p.b_mn);
+  const uint32_t idesc = p.fp8 ? idesc_e4m3(BM, p.N)
+                               : idesc_bf16(p.pair ? 2 * BM : BM, p.N, p.a_mn, p.b_mn);
   const uint32_t idesc_db = idesc_bf16(BM, 16, p.a_mn, false);
+  const uint32_t idesc_db2 = idesc_bf16(2 * BM, 16, p.a_mn, false);
   // an all-ones 16 x 16 BF16 block, no swizzle: every layout reads ones
   const uint64_t ones = smem_desc(smem_u32(s.ones), 128, 256, 0);
   uint32_t it = 0, lt = 0;
-  const int n_tiles = p.m_tiles * n_tn(p) * p.splits;
+  const int n_tiles = n_tiles_of(p);
   bool ok = true;
-  for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++lt) {
+  for (int t = first_tile(p); t < n_tiles && ok; t += tile_stride(p), ++lt) {
     int mt, nt, sp, nk;
     long long k0;
     tile_range(p, t, mt, nt, sp, k0, nk);
@@ -167,18 +220,36 @@ __device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
                                 : smem_desc(ba + 32 * k, 16, 1024, kSwizzle128);
         uint32_t acc = (kb | k) != 0;
         // both kinds take 32 bytes of K per instruction (16 BF16 or 32 E4M3)
-        if (p.fp8)
-          mma_fp8(d, adesc, bdesc, idesc, acc);
-        else
-          mma_bf16(d, adesc, bdesc, idesc, acc);
-        if (db_tile) mma_bf16(d + p.N, adesc, ones, idesc_db, acc);
+        if constexpr (kPair) {
+          mma_bf16_pair(d, adesc, bdesc, idesc, acc);
+          if (db_tile) mma_bf16_pair(d + p.N, adesc, ones, idesc_db2, acc);
+        } else {
+          if (p.fp8)
+            mma_fp8(d, adesc, bdesc, idesc, acc);
+          else
+            mma_bf16(d, adesc, bdesc, idesc, acc);
+          if (db_tile) mma_bf16(d + p.N, adesc, ones, idesc_db, acc);
+        }
       }
-      mma_commit(&s.empty[st]);
+      if constexpr (kPair)
+        mma_commit_pair_both(&s.empty[st]);
+      else
+        mma_commit(&s.empty[st]);
     }
-    if (ok) mma_commit(&s.tfull[ab]);
+    if (ok) {
+      if constexpr (kPair)
+        mma_commit_pair_both(&s.tfull[ab]);
+      else
+        mma_commit(&s.tfull[ab]);
+    }
   }
-  // all MMAs of this thread must have completed before TMEM is freed
-  mma_commit(s.drain);
+  // all MMAs of this thread must have completed before TMEM is freed (a
+  // pair's commit arrives on the drain barrier of both CTAs; only this
+  // one waits)
+  if constexpr (kPair)
+    mma_commit_pair_both(s.drain);
+  else
+    mma_commit(s.drain);
   mbar_wait(s.drain, 0, p.err, 4);
 }
 
@@ -202,13 +273,14 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
   const int q = warp & 3;              // TMEM lane quadrant this warp may access
   const int half = (warp - 2) / 4;     // which alternate 32-column chunks
   const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
-  const int n_tiles = p.m_tiles * n_tn(p) * p.splits;
+  const int n_tiles = n_tiles_of(p);
   const int n_chunks = (p.N + 31) / 32;
+  const int rank = p.pair ? (int)cluster_ctarank() : 0;
   uint32_t lt = 0, staged = 0;
-  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+  for (int t = first_tile(p); t < n_tiles; t += tile_stride(p), ++lt) {
     int mt, nt, sp, nk;
     long long k0;
-    tile_range(p, t, mt, nt, sp, k0, nk);
+    tile_range(p, t, mt, nt, sp, k0, nk, rank);
     const int n0 = nt * p.N;
     uint32_t ab = lt % n_acc, ar = lt / n_acc;
     const int r_in = q * 32 + lane;
@@ -370,32 +442,42 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
     }
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive(&s.tempty[ab]);
+    if (lane == 0) {
+      // the accumulator is free again: tell the CTA whose thread issues the MMAs
+      if (rank == 0)
+        mbar_arrive(&s.tempty[ab]);
+      else
+        mbar_arrive_remote(mapa_shared(smem_u32(&s.tempty[ab]), 0));
+    }
   }
   if (p.stage_out && lane == 0) bulk_wait_all();  // stores done before the CTA exits
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-              const __grid_constant__ CUtensorMap tout, const TcGemmArgs p) {
+// The body of both kernels (kPair: a cluster of two CTAs, see the header).
+template <bool kPair>
+__device__ __forceinline__ void gemm_cta(const CUtensorMap *ta, const CUtensorMap *tb,
+                                         const CUtensorMap *tout, const TcGemmArgs &p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   Smem s = carve(base, p);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int rank = kPair ? (int)cluster_ctarank() : 0;
   const int n_acc = 2 * acc_stride(p) <= 512 ? 2 : 1;
   uint32_t cols = 32;
   while (cols < (uint32_t)(n_acc * acc_stride(p))) cols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < p.stages; ++i) {
+      // (a pair's loads all count on the even CTA's barriers)
       mbar_init(&s.full[i], 1);
       mbar_init(&s.empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&s.tfull[i], 1);
-      mbar_init(&s.tempty[i], kEpiWarps);
+      // a pair's accumulator is released by the epilogue warps of both CTAs
+      mbar_init(&s.tempty[i], kPair ? 2 * kEpiWarps : kEpiWarps);
     }
     mbar_init(s.drain, 1);
     for (int i = 0; i < 2; ++i) mbar_init(&s.dotbar[i], kEpiWarps / 2);
@@ -406,25 +488,47 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = threadIdx.x; i < kOnesBytes / 4; i += blockDim.x) o[i] = 0x3F803F80u;  // 1.0, 1.0
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(s.tslot, cols);
+  if (warp == 1) {
+    if (kPair)
+      tmem_alloc_pair(s.tslot, cols);
+    else
+      tmem_alloc(s.tslot, cols);
+  }
   tc_fence_before();
   __syncthreads();
+  if (kPair) cluster_sync();  // both CTAs' barriers exist before either touches the other's
   tc_fence_after();
   const uint32_t tbase = *s.tslot;
 
   if (warp == 0) {
-    if (lane == 0) producer(&ta, &tb, p, s);
+    if (lane == 0) producer<kPair>(ta, tb, p, s);
   } else if (warp == 1) {
-    if (lane == 0) mma_issuer(p, s, tbase);
+    if (lane == 0 && rank == 0) mma_issuer<kPair>(p, s, tbase);
   } else {
-    epilogue(p, s, tbase, &tout);
+    epilogue(p, s, tbase, tout);
   }
   tc_fence_before();
   __syncthreads();
+  if (kPair) cluster_sync();  // no CTA frees TMEM or exits while its pair still signals it
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tbase, cols);
+    if (kPair)
+      tmem_dealloc_pair(tbase, cols);
+    else
+      tmem_dealloc(tbase, cols);
   }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+              const __grid_constant__ CUtensorMap tout, const TcGemmArgs p) {
+  gemm_cta<false>(&ta, &tb, &tout, p);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    k_tc_gemm_pair(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                   const __grid_constant__ CUtensorMap tout, const TcGemmArgs p) {
+  gemm_cta<true>(&ta, &tb, &tout, p);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -489,8 +593,14 @@ int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorM
     return (int)cudaErrorInvalidValue;
   if (a.fp8 && (a.epi != kTcFwd || a.a_mn || a.b_mn || a.with_db))
     return (int)cudaErrorInvalidValue;
+  // pair mode: weight gradients only (MN-major operands), an even number of
+  // 128-row M tiles and each CTA's half of N a whole number of 64-column boxes
+  if (a.pair && (a.epi != kTcDw || a.fp8 || !a.a_mn || !a.b_mn || a.m_tiles % 2 != 0 ||
+                 (a.N != 128 && a.N != 256)))
+    return (int)cudaErrorInvalidValue;
   a.a_bytes = BM * BK * 2;  // 128 rows x 128 bytes, or 2 MN-major boxes of 64 x 128 bytes
-  a.b_bytes = a.b_mn ? ((a.N + 63) / 64) * 8192 : a.N * BK * 2;
+  // MN-major B: 64-column boxes of 64 x 128 bytes (a pair CTA holds half of N)
+  a.b_bytes = a.b_mn ? (((a.pair ? a.N / 2 : a.N) + 63) / 64) * 8192 : a.N * BK * 2;
   const int fixed = kOnesBytes + 2048 /*dot buffer*/ + 1024 /*alignment*/ + 256 /*barriers*/ +
                     (a.stage_out ? kEpiWarps * 2 * kStageBytes : 0);
   const int budget = 220 * 1024;
@@ -498,13 +608,36 @@ int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorM
   a.stages = stages > 8 ? 8 : stages;
   if (a.stages < 2) return (int)cudaErrorInvalidValue;
   size_t smem = (size_t)a.stages * (a.a_bytes + a.b_bytes) + fixed;
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  if (a.pair) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_pair,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    // as many clusters as can be resident at once (a persistent launch
+    // with clusters that would wait for others to finish runs a tail); if
+    // the query fails, one per SM pair (extra clusters then run in a later
+    // wave, which costs time but nothing else)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (num_sms / 2), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    int max_clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&max_clusters, k_tc_gemm_pair, &cfg) != cudaSuccess ||
+        max_clusters < 1) {
+      cudaGetLastError();
+      max_clusters = num_sms / 2 > 0 ? num_sms / 2 : 1;
+    }
+    const int pair_tiles = (a.m_tiles + 1) / 2 * (a.n_tn > 1 ? a.n_tn : 1) * a.splits;
+    const int clusters = pair_tiles < max_clusters ? pair_tiles : max_clusters;
+    k_tc_gemm_pair<<<2 * clusters, kThreads, smem, st>>>(ta, tb, tout ? *tout : none, a);
+    return (int)cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return (int)e;
   int tiles = a.m_tiles * (a.n_tn > 1 ? a.n_tn : 1) * a.splits;
   int grid = tiles < num_sms ? tiles : num_sms;
-  CUtensorMap none;
-  memset(&none, 0, sizeof(none));
   k_tc_gemm<<<grid, kThreads, smem, st>>>(ta, tb, tout ? *tout : none, a);
   return (int)cudaGetLastError();
 }

@@ -68,6 +68,11 @@ struct TcGemmArgs {
   // launch geometry (filled by the launcher)
   int stages, a_bytes, b_bytes;
   int *err;              // device flag: nonzero when a bounded wait gave up
+  // kTcDw with MN-major A and B only: run on clusters of two CTAs (two SMs)
+  // whose tensor cores share one M = 256 MMA (tcgen05 .cta_group::2); needs
+  // an even m_tiles and N of 128 or 256. Results are bitwise those of the
+  // single-CTA kernel (the same products summed in the same order).
+  int pair;
 };
 
 // 2D BF16 tensor map over a row-major [rows][cols] array with row stride
@@ -82,7 +87,8 @@ bool make_tmap_u8(CUtensorMap *tm, const void *ptr, long long rows, long long co
 bool make_tmap_bf16_plain(CUtensorMap *tm, const void *ptr, long long rows, long long cols,
                           long long ld, int box_cols, int box_rows);
 
-// Launches over min(tiles, SMs) persistent CTAs. tout: the map of out for
+// Launches over min(tiles, SMs) persistent CTAs (pair mode: min(tiles,
+// resident two-CTA clusters) clusters). tout: the map of out for
 // stage_out (else null). Returns a cudaError_t.
 int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap *tout,
                    TcGemmArgs a, int num_sms, cudaStream_t st);

@@ -611,6 +611,14 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
     a.a_mn = 1;
     a.b_mn = 1;
     a.m_tiles = (W + 127) / 128;
+    // two-SM tiles (256 neurons) where the layer has an even number of
+    // 128-neuron tiles and its input splits into whole 64-column boxes per
+    // CTA: N = 256 tiles, or one N = 128 tile for inputs of up to 128
+    // columns (the layer-0 encoding; columns past in_cols read as zeros)
+    if (a.m_tiles % 2 == 0 && (in_cols <= 128 || in_cols % 256 == 0)) {
+      a.pair = 1;
+      if (in_cols <= 128) a.N = 128;
+    }
     a.splits = splits_for(ns, a.m_tiles * a.n_tn, t->num_sms);
     a.k_per_split = ((ns + a.splits - 1) / a.splits + 63) / 64 * 64;
     a.splits = (int)((ns + a.k_per_split - 1) / a.k_per_split);
