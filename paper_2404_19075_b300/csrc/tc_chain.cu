@@ -532,9 +532,50 @@ __device__ __forceinline__ void swish_layer(const ChainArgs &p, uint8_t *A, int 
   }
 }
 
+// Column sums of this warp's 32 rows of the last hidden layer (the BF16
+// values it has just written to the tile buffer) over its 64-column chunks
+// jc = half, half + 2, ...: lane l sums columns 64 jc + 2 l and 2 l + 1 over
+// the live rows, in FP32, into hsum (see ChainArgs::hsum).
+__device__ __forceinline__ void warp_column_sums(const ChainArgs &p, const uint8_t *A,
+                                                 long long tile, int q, int half, int lane) {
+  if (tile >= p.m_tiles) return;  // a slot with no tile (its rows are all past ns)
+  const long long row0 = tile * 128 + q * 32;
+  const long long left = p.ns - row0;
+  const int n = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
+  for (int jc = half; jc < p.W / 64; jc += 2) {
+    const uint8_t *chunk = A + (size_t)jc * kChunkBytes + (lane & 3) * 4;
+    float2 acc = make_float2(0.0f, 0.0f);
+    if (n == 32) {
+      // all 32 rows' words in flight together, then a pairwise sum (the
+      // sum sits on the path to the slot's next tile)
+      uint32_t w[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        w[i] = *reinterpret_cast<const uint32_t *>(chunk + swz(q * 32 + i, lane >> 2));
+      float2 t[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        t[i] = add2(make_float2(bf_lo(w[2 * i]), bf_hi(w[2 * i])),
+                    make_float2(bf_lo(w[2 * i + 1]), bf_hi(w[2 * i + 1])));
+#pragma unroll
+      for (int k = 8; k > 0; k >>= 1)
+#pragma unroll
+        for (int i = 0; i < k; ++i) t[i] = add2(t[i], t[i + k]);
+      acc = t[0];
+    } else {
+      for (int i = 0; i < n; ++i) {
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(chunk + swz(q * 32 + i, lane >> 2));
+        acc = add2(acc, make_float2(bf_lo(w), bf_hi(w)));
+      }
+    }
+    *reinterpret_cast<float2 *>(p.hsum + (tile * 4 + q) * p.W + 64 * jc + 2 * lane) = acc;
+  }
+}
+
 // After layer L of one tile: bias + activation, BF16 back into the tile
-// buffer, ReLU bits (or the Swish derivative), TMA store of h_L, and on the
-// last layer the output dot product.
+// buffer, ReLU bits (or the Swish derivative), TMA store of h_L (on the last
+// layer with hsum set, the column sums instead), and on the last layer the
+// output dot product.
 template <int kAct>
 __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
                                int slot, uint32_t tcol, int L, long long tile, int q, int half,
@@ -585,12 +626,14 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
   }
   fence_async_smem();
   __syncwarp();
-  if (lane == 0 && p.store_h && tile * 128 + q * 32 < p.ns) {
+  const bool sums = last && p.hsum;
+  if (lane == 0 && p.store_h && !sums && tile * 128 + q * 32 < p.ns) {
     for (int jc = half; jc < p.W / 64; jc += 2)
       tma_store_2d(&maps.h[L], A + (size_t)jc * kChunkBytes + q * 32 * 128, 64 * jc,
                    (int)(tile * 128 + q * 32));
     bulk_commit();
   }
+  if (sums) warp_column_sums(p, A, tile, q, half, lane);
   if (last) {
     float *db = s.dot + slot * 128;
     if (half == 1) {

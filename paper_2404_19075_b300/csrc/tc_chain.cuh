@@ -48,6 +48,12 @@ struct ChainArgs {
   int m_tiles;
   int stages;
   int store_h;                     // write h_L to HBM (training) or not (queries)
+  // Training with every tile inside one ray and an identity output: instead
+  // of storing h_{H-1} (read only by the output-layer weight gradient), the
+  // forward writes, per tile and TMEM lane quadrant q, the column sums of
+  // h_{H-1} (its BF16 values) over the quadrant's live rows,
+  // hsum[(tile * 4 + q) * W + c]; null: h_{H-1} is stored like the others.
+  float *hsum;
   const float *bias[kChainMaxLayers];
   const float *w_out, *b_out;
   float *z_out;                    // [ns]

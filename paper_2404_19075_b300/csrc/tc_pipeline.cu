@@ -50,6 +50,11 @@ struct TcState {
   float *ones = nullptr;          // 1.0 [samples], allocated when serving starts
   bool chain = false;
   float *zpart = nullptr;         // [N tiles][samples] partial output dots (W > 256)
+  // [tiles][4][W] column sums of h_{H-1} per TMEM lane quadrant (chain path,
+  // see ChainArgs::hsum); hsum_used: the last training forward wrote them
+  // in place of h_{H-1}
+  float *hsum = nullptr;
+  bool hsum_used = false;
   // FP8 forward (DINR_PREC_FP8): E4M3 copies of the features, of two
   // consecutive hidden outputs and of the weights, and per-tensor scales
   // fscale = [1 (features), s_w[H], s_h[H]] with amax records.
@@ -232,6 +237,32 @@ __global__ void __launch_bounds__(256)
       part[(long long)z * C + 8 * threadIdx.x + k] = s;
     }
   }
+}
+
+// part[z][c] = sum over the rows r of split z of dz[128 (r / 4)] hsum[r][c]
+// (r = 4 tile + quadrant): the output-layer weight gradient from the forward
+// chain's column sums of h_{H-1} per tile quadrant, when dz is constant over
+// every tile. One thread per column; eight rows in flight per thread.
+__global__ void __launch_bounds__(256)
+    k_tilesum_grad(const float *hsum, int W, long long rows, const float *dz, int splits,
+                   float *part) {
+  const int z = blockIdx.x, c = threadIdx.x;
+  const long long per = (rows + splits - 1) / splits;
+  const long long r0 = z * per, r1 = r0 + per < rows ? r0 + per : rows;
+  float acc = 0.0f;
+  long long r = r0;
+  for (; r + 8 <= r1; r += 8) {
+    float h[8], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      h[k] = __ldcs(hsum + (r + k) * W + c);
+      d[k] = dz[((r + k) >> 2) * 128];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc = fmaf(d[k], h[k], acc);
+  }
+  for (; r < r1; ++r) acc = fmaf(dz[(r >> 2) * 128], hsum[r * W + c], acc);
+  part[(long long)z * W + c] = acc;
 }
 
 // Blocks of the output-layer column sum: at most one full wave (SMs x the
@@ -490,6 +521,13 @@ dinr_status chain(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S, b
   a.m_tiles = (int)((ns + 127) / 128);
   a.stages = chain_stages(c->W, a.k0);
   a.store_h = store_h ? 1 : 0;
+  // training rays whose samples fill whole tiles and an identity output: dz
+  // is constant over each tile, so the output-layer weight gradient needs
+  // only the column sums of h_{H-1} per tile
+  const bool sums = store_h && t->hsum && src.kind == kSrcTrainRays && S % 128 == 0 &&
+                    c->out_act == DINR_OUT_IDENTITY;
+  a.hsum = sums ? t->hsum : nullptr;
+  if (store_h) t->hsum_used = sums;
   for (int L = 0; L < c->H; ++L) a.bias[L] = c->d_params + c->offb[L];
   a.w_out = c->d_params + c->offW[c->H];
   a.b_out = c->d_params + c->offb[c->H];
@@ -511,7 +549,9 @@ dinr_status chain(dinr_ctx *c, const SourceArgs &src, long long n_rays, int S, b
   }
   double pw = (double)c->W * c->d_in + (double)(c->H - 1) * c->W * c->W + c->W;
   ProfScope ps(c, "tc_fwd_chain", 2.0 * ns * pw,
-               store_h ? 2.0 * ns * (c->ldE + (double)c->H * c->W) : 4.0 * ns);
+               store_h ? 2.0 * ns * (c->ldE + (double)(sums ? c->H - 1 : c->H) * c->W) +
+                             (sums ? 16.0 * a.m_tiles * c->W : 0.0)
+                       : 4.0 * ns);
   int e = launch_fwd_chain(maps, a, t->num_sms, c->st);
   ++c->launches;
   if (e != 0)
@@ -575,7 +615,20 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
   }
   int cs = colsum_bf16_splits(t->num_sms, ns);
   dinr_status s;
-  {
+  if (t->chain && t->hsum_used) {
+    // from the forward chain's column sums of h_{H-1}: dz is constant over a tile
+    const long long rows = (ns + 127) / 128 * 4;
+    const int ts = t->num_sms * 2;
+    ProfScope ps(c, "dw_out", 2.0 * rows * W, 4.0 * rows * W + 4.0 * rows / 4);
+    k_tilesum_grad<<<ts, W, 0, c->st>>>(t->hsum, W, rows, t->dz, ts, t->part);
+    CKL();
+    s = reduce_into(c, t->part, ts, W, c->offW[c->H], acc);
+    if (s != DINR_OK) return s;
+    launch_colsum(t->dz, 1, 1, ns, nullptr, false, 0, cs, t->part, c->st);
+    CKL();
+    s = reduce_into(c, t->part, cs, 1, c->offb[c->H], acc);
+    if (s != DINR_OK) return s;
+  } else {
     ProfScope ps(c, "dw_out", 2.0 * ns * W, 2.0 * ns * W + 4.0 * ns);
     k_colsum_bf16<<<cs, 256, 0, c->st>>>(hH, W, ns, t->dz, cs, t->part);
     CKL();
@@ -700,7 +753,7 @@ bool tc_recompute_applies(const dinr_ctx *c) {
 
 long long tc_bytes_per_sample(const dinr_ctx *c) {
   if (chains_used(c))
-    return 2LL * (c->ldE + 2LL * c->H * c->W) + 32 + 8 + 16 +
+    return 2LL * (c->ldE + 2LL * c->H * c->W) + 32 + 8 + 16 + c->W / 8 /*hsum*/ +
            (c->act == DINR_ACT_SWISH ? 2LL * c->H * c->W : (long long)c->H * c->W / 8);
   return 2LL * (c->ldE + (long long)(n_hbuf(c) * (c->act == DINR_ACT_SWISH ? 2 : 1) + 2) * c->W) +
          8 + 16 +
@@ -744,7 +797,8 @@ dinr_status tc_alloc(dinr_ctx *c) {
          (c->act == DINR_ACT_SWISH
               ? grab((void **)&t->G, 2ull * ns_tiles * c->W * c->H)
               : grab((void **)&t->masks, 4ull * ns_tiles * (c->W / 32) * c->H)) &&
-         grab((void **)&t->rec, 32ull * ns);
+         grab((void **)&t->rec, 32ull * ns) &&
+         grab((void **)&t->hsum, 4ull * (ns_tiles / 128) * 4 * c->W);
   else
     ok = ok && grab((void **)&t->D0, 2ull * ns * c->W) && grab((void **)&t->D1, 2ull * ns * c->W);
   t->owner.assign(n_hbuf(c), -1);
