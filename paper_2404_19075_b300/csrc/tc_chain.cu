@@ -144,6 +144,16 @@ __device__ __forceinline__ uint32_t *mask_unit(const ChainArgs &p, int L, long l
   return p.masks[L] + (((row >> 7) * (p.W / 64) + jc) << 8) + ((row & 127) << 1);
 }
 
+// lo += low BF16 half of w, hi += high half, each in FP32 with one rounding
+// (the mixed-precision add of sm_100 and later; the halves are register
+// halves, so no unpacking).
+__device__ __forceinline__ void add_bf16x2(float &lo, float &hi, uint32_t w) {
+  asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+      "add.rn.f32.bf16 %0, l, %0;\n\tadd.rn.f32.bf16 %1, h, %1;\n\t}"
+      : "+f"(lo), "+f"(hi)
+      : "r"(w));
+}
+
 // Low / high BF16 half of a packed pair, as FP32.
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
@@ -546,26 +556,20 @@ __device__ __forceinline__ void warp_column_sums(const ChainArgs &p, const uint8
     const uint8_t *chunk = A + (size_t)jc * kChunkBytes + (lane & 3) * 4;
     float2 acc = make_float2(0.0f, 0.0f);
     if (n == 32) {
-      // all 32 rows' words in flight together, then a pairwise sum (the
-      // sum sits on the path to the slot's next tile)
+      // all 32 rows' words in flight together, summed in four independent
+      // chains per column (the sum sits on the path to the slot's next tile)
       uint32_t w[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i)
         w[i] = *reinterpret_cast<const uint32_t *>(chunk + swz(q * 32 + i, lane >> 2));
-      float2 t[16];
+      float lo[4] = {0.0f, 0.0f, 0.0f, 0.0f}, hi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        t[i] = add2(make_float2(bf_lo(w[2 * i]), bf_hi(w[2 * i])),
-                    make_float2(bf_lo(w[2 * i + 1]), bf_hi(w[2 * i + 1])));
-#pragma unroll
-      for (int k = 8; k > 0; k >>= 1)
-#pragma unroll
-        for (int i = 0; i < k; ++i) t[i] = add2(t[i], t[i + k]);
-      acc = t[0];
+      for (int i = 0; i < 32; ++i) add_bf16x2(lo[i & 3], hi[i & 3], w[i]);
+      acc = make_float2((lo[0] + lo[1]) + (lo[2] + lo[3]), (hi[0] + hi[1]) + (hi[2] + hi[3]));
     } else {
       for (int i = 0; i < n; ++i) {
         const uint32_t w = *reinterpret_cast<const uint32_t *>(chunk + swz(q * 32 + i, lane >> 2));
-        acc = add2(acc, make_float2(bf_lo(w), bf_hi(w)));
+        add_bf16x2(acc.x, acc.y, w);
       }
     }
     *reinterpret_cast<float2 *>(p.hsum + (tile * 4 + q) * p.W + 64 * jc + 2 * lane) = acc;
