@@ -70,6 +70,17 @@ __device__ __forceinline__ uint32_t swz(int r, int c16) {
   return (uint32_t)(r * 128 + ((c16 ^ (r & 7)) << 4));
 }
 
+// TMEM store of 32 consecutive columns of this warp's 32 lanes (one value
+// per lane and column), and the wait for this thread's TMEM stores.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
   __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t *>(&v);
@@ -286,7 +297,8 @@ __device__ void mma_issuer(const ChainArgs &p, const Smem &s, uint32_t tbase) {
           for (int k = 0; k < 4; ++k) {
             uint64_t ad = smem_desc(a0 + kc * kChunkBytes + 32 * k, 16, 1024, kSwizzle128);
             uint64_t bd = smem_desc(b0 + 32 * k, 16, 1024, kSwizzle128);
-            mma_bf16(d, ad, bd, idesc, (kc | k) != 0);
+            // forward: the accumulator already holds the layer's bias
+            mma_bf16(d, ad, bd, idesc, !kBwd || (kc | k) != 0);
           }
           mma_commit(&s.empty[st]);
         }
@@ -473,25 +485,18 @@ __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *
 }
 
 // Swish part of the forward epilogue for the 32 columns c0 .. c0 + 31 whose
-// accumulators are in r: h = swish(z) into the tile buffer, the derivative
-// g into gact[L] (the backward's factor in place of the ReLU mask), and on
-// the last layer the output dot product.
+// pre-activations z (the accumulator started from the bias) are in r:
+// h = swish(z) into the tile buffer, the derivative g into gact[L] (the
+// backward's factor in place of the ReLU mask), and on the last layer the
+// output dot product.
 __device__ __forceinline__ void swish_group(const ChainArgs &p, uint8_t *A, int L, int c0,
                                             const uint32_t (&r)[32], int r_in, uint8_t *gbase,
                                             bool last, float &dot) {
-  const float *bias = p.bias[L] + c0;
-  float4 bb[8];
-#pragma unroll
-  for (int i4 = 0; i4 < 8; ++i4) bb[i4] = ld_keep(bias + 4 * i4);
   uint32_t wh[16], wg[16];
 #pragma unroll
   for (int i4 = 0; i4 < 8; ++i4) {
-    const float4 b = bb[i4];
-    const float2 z0 = add2(make_float2(__uint_as_float(r[4 * i4]), __uint_as_float(r[4 * i4 + 1])),
-                           make_float2(b.x, b.y));
-    const float2 z1 = add2(make_float2(__uint_as_float(r[4 * i4 + 2]),
-                                       __uint_as_float(r[4 * i4 + 3])),
-                           make_float2(b.z, b.w));
+    const float2 z0 = make_float2(__uint_as_float(r[4 * i4]), __uint_as_float(r[4 * i4 + 1]));
+    const float2 z1 = make_float2(__uint_as_float(r[4 * i4 + 2]), __uint_as_float(r[4 * i4 + 3]));
     float2 h0, h1;
     swish_pair(z0, h0, wh[2 * i4], wg[2 * i4]);
     swish_pair(z1, h1, wh[2 * i4 + 1], wg[2 * i4 + 1]);
@@ -576,36 +581,55 @@ __device__ __forceinline__ void warp_column_sums(const ChainArgs &p, const uint8
   }
 }
 
-// After layer L of one tile: bias + activation, BF16 back into the tile
-// buffer, ReLU bits (or the Swish derivative), TMA store of h_L (on the last
-// layer with hsum set, the column sums instead), and on the last layer the
-// output dot product.
+// The bias of the next MMA into this warp's TMEM lanes and 64-column chunks
+// (half, half + 2, ...) of a tile slot, whose accumulator the epilogue has
+// just read: the next layer's MMAs then accumulate onto it, so the epilogue
+// adds no bias.
+__device__ __forceinline__ void tmem_put_bias(const float *bias, uint32_t trow, int half, int W) {
+  for (int jc = half; jc < W / 64; jc += 2) {
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      uint32_t r[32];
+#pragma unroll
+      for (int i4 = 0; i4 < 8; ++i4) {
+        const float4 b = ld_keep(bias + 64 * jc + 32 * hh + 4 * i4);
+        r[4 * i4] = __float_as_uint(b.x);
+        r[4 * i4 + 1] = __float_as_uint(b.y);
+        r[4 * i4 + 2] = __float_as_uint(b.z);
+        r[4 * i4 + 3] = __float_as_uint(b.w);
+      }
+      tmem_st32(trow + 64 * jc + 32 * hh, r);
+    }
+  }
+  tmem_wait_st();
+}
+
+// After layer L of one tile: activation of the accumulator (which started
+// from the bias), BF16 back into the tile buffer, ReLU bits (or the Swish
+// derivative), TMA store of h_L (on the last layer with hsum set, the column
+// sums instead), on the last layer the output dot product; then next_bias
+// (the slot's next layer, or layer 0 of its next tile; null if none) into
+// the accumulator.
 template <int kAct>
 __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const Smem &s,
                                int slot, uint32_t tcol, int L, long long tile, int q, int half,
-                               int lane, uint32_t dot_phase) {
+                               int lane, uint32_t dot_phase, const float *next_bias) {
   const int r_in = q * 32 + lane;
   const long long row = tile * 128 + r_in;
   const bool live = row < p.ns;
   const bool last = L == p.H - 1;
   const uint32_t trow = tcol + ((uint32_t)(q * 32) << 16);
-  const float *bias = p.bias[L];
   uint8_t *A = s.A[slot];
   float dot = 0.0f;
   if constexpr (kAct == kActSwish) swish_layer(p, A, L, trow, r_in, row, live, last, half, dot);
   for (int jc = half; kAct != kActSwish && jc < p.W / 64; jc += 2) {
-    // bias of the chunk first, so that its load overlaps the TMEM load
-    float4 bb[16];
-#pragma unroll
-    for (int i4 = 0; i4 < 16; ++i4) bb[i4] = ld_keep(bias + 64 * jc + 4 * i4);
     float v[64];
     tmem_ld64(trow + 64 * jc, v);
     uint32_t w[32];
 #pragma unroll
     for (int i4 = 0; i4 < 16; ++i4) {
-      const float4 b = bb[i4];
-      const float2 s0 = add2(make_float2(v[4 * i4], v[4 * i4 + 1]), make_float2(b.x, b.y));
-      const float2 s1 = add2(make_float2(v[4 * i4 + 2], v[4 * i4 + 3]), make_float2(b.z, b.w));
+      const float2 s0 = make_float2(v[4 * i4], v[4 * i4 + 1]);
+      const float2 s1 = make_float2(v[4 * i4 + 2], v[4 * i4 + 3]);
       w[2 * i4] = pack2_relu(s0.x, s0.y);
       w[2 * i4 + 1] = pack2_relu(s1.x, s1.y);
       if (last) {
@@ -628,6 +652,7 @@ __device__ bool epilogue_layer(const ChainMaps &maps, const ChainArgs &p, const 
       if (live) st_stream2(mask_unit(p, L, row, jc), make_uint2(bits[0], bits[1]));
     }
   }
+  if (next_bias) tmem_put_bias(next_bias, trow, half, p.W);
   fence_async_smem();
   __syncwarp();
   const bool sums = last && p.hsum;
@@ -884,6 +909,13 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
   if (np == 0) return;
   for (int slot = 0; slot < 2; ++slot) {
     start_tile(slot, tile_of(p, 0, slot));
+    if (!kBwd) {
+      // the first layer's bias into the slot's accumulator
+      tmem_put_bias(p.bias[0], tbase + (uint32_t)(slot * p.W) + ((uint32_t)(q * 32) << 16), half,
+                    p.W);
+      tc_fence_before();
+    }
+    __syncwarp();
     if (lane == 0) mbar_arrive(&s.aready[slot]);
   }
   for (int pr = 0; pr < np; ++pr)
@@ -900,8 +932,9 @@ __device__ void epilogue_warps(const ChainMaps &maps, const ChainArgs &p, const 
           if (!warp_wait(&s.tfull[slot], waits[slot]++ & 1, p.err, 17)) return;
           tc_fence_after();
           wait_stores();
+          const float *nb = i + 1 < ns ? p.bias[i + 1] : (pr + 1 < np ? p.bias[0] : nullptr);
           if (!epilogue_layer<kAct>(maps, p, s, slot, tcol, i, tile, q, half, lane,
-                              last ? dots[slot]++ : 0))
+                              last ? dots[slot]++ : 0, nb))
             return;
         }
         tc_fence_before();
