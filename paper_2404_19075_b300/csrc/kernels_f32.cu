@@ -76,8 +76,14 @@ __device__ __forceinline__ void store_tile(float (*S)[BM + 4], const float (&reg
   }
 }
 
+// Blocked summation (below) in the forward and weight-gradient GEMMs; the
+// input-gradient GEMMs (K = layer width) sum straight into the accumulators
+// and keep two blocks per SM resident. (Without blocking in the forward as
+// well, the layer-0 weight gradient of a 128-ray parallel-beam subset left
+// the 1e-5 bound against the FP64 oracle: 2.3e-5 norm-wise.)
 template <bool A_KC, bool B_KC, bool A_ACT, bool B_ACT, int EPI>
-__global__ void __launch_bounds__(256) k_sgemm(SgemmArgs a) {
+__global__ void __launch_bounds__(256, EPI != kEpiMask ? 1 : 2) k_sgemm(SgemmArgs a) {
+  constexpr bool kBlocked = EPI != kEpiMask;
   __shared__ __align__(16) float As[2][BK][BM + 4];
   __shared__ __align__(16) float Bs[2][BK][BN + 4];
   int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -92,14 +98,16 @@ __global__ void __launch_bounds__(256) k_sgemm(SgemmArgs a) {
 
   // Blocked summation: products are accumulated in blocks of kBlockK terms
   // and each block is added into the total, which keeps the rounding growth
-  // near kBlockK + K/kBlockK instead of K (K is 256 for hidden layers and
-  // thousands of samples for weight gradients).
+  // near kBlockK + K/kBlockK instead of K (thousands of samples for weight
+  // gradients).
   constexpr int kBlockK = 32;
-  float tot[8][8];
+  float tot[8][8];  // (unused, and removed, without blocking)
+  if constexpr (kBlocked) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) tot[i][j] = 0.0f;
+      for (int j = 0; j < 8; ++j) tot[i][j] = 0.0f;
+  }
 
   float ra[8], rb[8];
   load_tile<A_KC>(a.A, a.lda, a.M, kb, ke, m0, A_ACT, a.act, ra);
@@ -127,14 +135,16 @@ __global__ void __launch_bounds__(256) k_sgemm(SgemmArgs a) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    if (((k0 - kb) / BK + 1) % (kBlockK / BK) == 0 || !more) {
+    if constexpr (kBlocked) {
+      if (((k0 - kb) / BK + 1) % (kBlockK / BK) == 0 || !more) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          tot[i][j] += acc[i][j];
-          acc[i][j] = 0.0f;
-        }
+          for (int j = 0; j < 8; ++j) {
+            tot[i][j] += acc[i][j];
+            acc[i][j] = 0.0f;
+          }
+      }
     }
     if (more) {
       // the other buffer was last read before the previous barrier
@@ -156,7 +166,9 @@ __global__ void __launch_bounds__(256) k_sgemm(SgemmArgs a) {
       // four consecutive columns of the row: 16-byte loads and stores when
       // they are all inside and aligned
       const int n = n0 + jh * 64 + tx * 4;
-      float v[4] = {tot[i][4 * jh], tot[i][4 * jh + 1], tot[i][4 * jh + 2], tot[i][4 * jh + 3]};
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = kBlocked ? tot[i][4 * jh + e] : acc[i][4 * jh + e];
       float *dst = C + (long long)m * a.ldc + n;
       const float *zp = EPI == kEpiMask ? a.Zp + (long long)m * a.ldz + n : nullptr;
       const bool vec = n + 4 <= a.N && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 &&
