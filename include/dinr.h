@@ -195,6 +195,13 @@ DINR_API dinr_status dinr_set_projections(dinr_ctx *ctx, const float *proj, int 
  *   n:       1..train.batch_rays.
  *   loss_out: host pointer that receives L; the call then waits for the
  *            step. NULL: no wait, the loss stays on the device.
+ * Host indices are read before the call returns (pinned memory included:
+ * with loss_out the call waits; without it, it waits for their copy).
+ * With host indices and loss_out (and neither the App. A forward model
+ * nor profiling) the step runs as one launch of a CUDA graph of the step,
+ * captured at the first such call for each n on a private stream and
+ * ordered after and before the context stream's work by events; the
+ * result is bitwise that of the ordinary launches.
  * Errors: DINR_ERR_ARG (n out of range; a host index outside [0, M*N); a
  * device index outside it is replaced by 0 and reported when the call
  * waits), DINR_ERR_NONFINITE (loss_out given and L is not finite; the

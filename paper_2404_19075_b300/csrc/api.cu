@@ -318,6 +318,7 @@ void dinr_destroy(dinr_ctx *c) {
   dinr_serve_release(c);
   if (c->gst) cudaStreamSynchronize(c->gst);  // replays in flight finish first
   if (c->gexec) cudaGraphExecDestroy((cudaGraphExec_t)c->gexec);
+  if (c->gexec_staged) cudaGraphExecDestroy((cudaGraphExec_t)c->gexec_staged);
   for (cudaEvent_t e : c->gev)
     if (e) cudaEventDestroy(e);
   if (c->gst) cudaStreamDestroy(c->gst);
@@ -425,9 +426,16 @@ dinr_status dinr_backward(dinr_ctx *c, const float *dloss_dev, float *grad_dev) 
   return DINR_OK;
 }
 
+static dinr_status train_step_staged(dinr_ctx *c, const int64_t *idx, int n, float *loss_out);
+
 dinr_status dinr_train_step(dinr_ctx *c, const int64_t *idx, int n, int on_device,
                             float *loss_out) {
   LIVE(c);
+  // host indices with the loss read back: one graph launch per step (not
+  // for App. A passes, which read sample counts back, or when profiling,
+  // which times every launch)
+  if (idx && !on_device && loss_out && c->geo.D == 0 && !c->prof)
+    return train_step_staged(c, idx, n, loss_out);
   dinr_status s = stage_indices(c, idx, n, on_device);
   if (s != DINR_OK) return s;
   s = run_loss_grad(c, n);
@@ -474,14 +482,19 @@ static void step_scalars(const dinr_ctx *c, long long step, int n, float *out) {
 // Captures one training step of n sampled rays on the private stream: the
 // sampler reading the device step counter, loss and gradient, Adam from
 // the table, the parameter copies, the counter's increment.
-static dinr_status capture_step(dinr_ctx *c, int n) {
+// Capture one training step of n rays into a graph: with `sampled` its
+// minibatch comes from the device sampler (dinr_train_graph), otherwise
+// from the indices already staged in d_idx (host indices of
+// dinr_train_step).
+static dinr_status capture_step(dinr_ctx *c, int n, bool sampled) {
   if (!c->gst) {
     CK(cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking));
     for (cudaEvent_t &e : c->gev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
-  if (c->gexec) {
-    cudaGraphExecDestroy((cudaGraphExec_t)c->gexec);
-    c->gexec = nullptr;
+  void *&slot = sampled ? c->gexec : c->gexec_staged;
+  if (slot) {
+    cudaGraphExecDestroy((cudaGraphExec_t)slot);
+    slot = nullptr;
   }
   cudaStream_t user = c->st;
   const long long launches = c->launches;  // captured launches run only when replayed
@@ -489,8 +502,10 @@ static dinr_status capture_step(dinr_ctx *c, int n) {
   cudaError_t e = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeRelaxed);
   dinr_status s = DINR_OK;
   if (e == cudaSuccess) {
-    launch_sample_indices_dev(c->n_proj, n, c->d_step, c->sampler_seed, c->d_idx, c->st);
-    ++c->launches;
+    if (sampled) {
+      launch_sample_indices_dev(c->n_proj, n, c->d_step, c->sampler_seed, c->d_idx, c->st);
+      ++c->launches;
+    }
     s = run_loss_grad(c, n);
     if (s == DINR_OK) {
       launch_adam_tab(c->d_params, c->d_m, c->d_v, c->d_grad, c->P, (float)c->b1, (float)c->b2,
@@ -529,9 +544,69 @@ static dinr_status capture_step(dinr_ctx *c, int n) {
   cudaGraphDestroy(g);
   if (e != cudaSuccess)
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "step graph: %s", cudaGetErrorString(e));
-  c->gexec = ex;
-  c->g_rays = n;
-  c->g_kernels = kernels;
+  slot = ex;
+  (sampled ? c->g_rays : c->gs_rays) = n;
+  (sampled ? c->g_kernels : c->gs_kernels) = kernels;
+  return DINR_OK;
+}
+
+// The device step counter and the Adam scalar table of graph-replayed steps
+// (room for at least `steps` steps).
+static dinr_status graph_state(dinr_ctx *c, int steps) {
+  bool ok = true;
+  if (!c->d_step) {
+    c->d_step = (long long *)dev_alloc(c, 2 * sizeof(long long), &ok);
+    if (ok) c->d_step0 = c->d_step + 1;
+  }
+  if (ok && steps > c->sched_cap) {
+    const int cap = steps > 1024 ? steps : 1024;
+    c->d_sched = (float *)dev_alloc(c, sizeof(float) * 3 * (size_t)cap, &ok);
+    if (ok) c->sched_cap = cap;
+  }
+  if (!ok) return (dinr_status)dinr_fail(c, DINR_ERR_OOM, "step graph state: out of memory");
+  return DINR_OK;
+}
+
+// dinr_train_step with host indices and the loss read back: the indices are
+// copied in, then the step is replayed from a graph captured once per
+// minibatch size (the same kernels, in the same order, as the ordinary
+// step: bitwise the same result, without a launch per kernel per step).
+static dinr_status train_step_staged(dinr_ctx *c, const int64_t *idx, int n, float *loss_out) {
+  if (n < 1 || n > c->batch_rays)
+    return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "n = %d outside [1, %d]", n, c->batch_rays);
+  for (int i = 0; i < n; ++i)
+    if (idx[i] < 0 || idx[i] >= c->n_proj)
+      return (dinr_status)dinr_fail(c, DINR_ERR_ARG, "ray index %lld outside [0, %lld)",
+                                    (long long)idx[i], c->n_proj);
+  c->fwd_n = 0;
+  c->fwd_kept = false;
+  dinr_status s = graph_state(c, 1);
+  if (s != DINR_OK) return s;
+  // the caller's indices may sit in pinned memory, whose copy runs later:
+  // this call returns only after the step (and so the copy) has completed
+  CK(cudaMemcpyAsync(c->d_idx, idx, sizeof(long long) * n, cudaMemcpyHostToDevice, c->st));
+  float tab[3];
+  step_scalars(c, c->step, n, tab);
+  const long long s0[2] = {c->step, c->step};
+  // pageable host sources: each copy has taken its bytes when it returns
+  CK(cudaMemcpyAsync(c->d_sched, tab, sizeof(tab), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->d_step, s0, sizeof(s0), cudaMemcpyHostToDevice, c->st));
+  if (!c->gexec_staged || c->gs_rays != n) {
+    s = capture_step(c, n, false);
+    if (s != DINR_OK) return s;
+  }
+  CK(cudaEventRecord(c->gev[0], c->st));
+  CK(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
+  CK(cudaGraphLaunch((cudaGraphExec_t)c->gexec_staged, c->gst));
+  CK(cudaEventRecord(c->gev[1], c->gst));
+  CK(cudaStreamWaitEvent(c->st, c->gev[1], 0));
+  c->step += 1;
+  c->launches += c->gs_kernels;
+  CK(cudaMemcpyAsync(loss_out, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  s = backend_poll(c);
+  if (s != DINR_OK) return s;
+  if (!std::isfinite(*loss_out))
+    return (dinr_status)dinr_fail(c, DINR_ERR_NONFINITE, "loss is not finite");
   return DINR_OK;
 }
 
@@ -551,17 +626,8 @@ dinr_status dinr_train_graph(dinr_ctx *c, int n, int steps, float *loss_out) {
   }
   c->fwd_n = 0;  // the graph restages the minibatch indices
   c->fwd_kept = false;
-  bool ok = true;
-  if (!c->d_step) {
-    c->d_step = (long long *)dev_alloc(c, 2 * sizeof(long long), &ok);
-    if (ok) c->d_step0 = c->d_step + 1;
-  }
-  if (ok && steps > c->sched_cap) {
-    const int cap = steps > 1024 ? steps : 1024;
-    c->d_sched = (float *)dev_alloc(c, sizeof(float) * 3 * (size_t)cap, &ok);
-    if (ok) c->sched_cap = cap;
-  }
-  if (!ok) return (dinr_status)dinr_fail(c, DINR_ERR_OOM, "step graph state: out of memory");
+  dinr_status gs = graph_state(c, steps);
+  if (gs != DINR_OK) return gs;
   std::vector<float> tab(3 * (size_t)steps);
   for (int k = 0; k < steps; ++k) step_scalars(c, c->step + k, n, &tab[3 * (size_t)k]);
   const long long s0[2] = {c->step, c->step};
@@ -570,7 +636,7 @@ dinr_status dinr_train_graph(dinr_ctx *c, int n, int steps, float *loss_out) {
                      c->st));
   CK(cudaMemcpyAsync(c->d_step, s0, sizeof(s0), cudaMemcpyHostToDevice, c->st));
   if (!c->gexec || c->g_rays != n) {
-    dinr_status s = capture_step(c, n);
+    dinr_status s = capture_step(c, n, true);
     if (s != DINR_OK) return s;
   }
   CK(cudaEventRecord(c->gev[0], c->st));

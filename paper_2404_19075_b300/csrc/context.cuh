@@ -70,6 +70,11 @@ struct dinr_ctx {
   void *gexec = nullptr;          // cudaGraphExec_t of one step
   int g_rays = 0;                 // minibatch size it was captured for
   long long g_kernels = 0;        // kernel nodes of the graph
+  // the same for a step on indices already staged in d_idx (host indices
+  // of dinr_train_step): no sampler kernel
+  void *gexec_staged = nullptr;
+  int gs_rays = 0;
+  long long gs_kernels = 0;
   cudaStream_t gst = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
 

@@ -71,3 +71,26 @@ def test_graph_call_runs_app_a_steps_as_ordinary_steps():
         finally:
             m.close()
     assert out[0] == out[1]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_host_index_steps_replayed_equal_ordinary_steps(prec):
+    """Host-index steps that read the loss back run as one graph launch each
+    (captured once per minibatch size); without the loss read-back they run
+    as ordinary launches. Both must give bitwise the same state, across an
+    epoch boundary of the App. C decay and a change of minibatch size."""
+    require_gpu()
+    a, b = _pair(prec)
+    rng = np.random.default_rng(11)
+    try:
+        for k in range(7):
+            n = 512 if k < 5 else 384
+            idx = torch.from_numpy(rng.integers(0, 2048, n)).pin_memory()
+            la = a.train_step_host(idx, sync=True)        # graph replay
+            b.train_step_host(idx, sync=False)             # ordinary launches
+            assert la == b.loss()
+        assert torch.equal(a.params(), b.params())
+        assert a.get_state() == b.get_state()
+    finally:
+        a.close()
+        b.close()
