@@ -125,26 +125,38 @@ __device__ __forceinline__ uint2 ld_stream2(const uint32_t *p) {
                : "l"(p));
   return v;
 }
-__device__ __forceinline__ uint4 ld_stream16(const void *p) {
-  uint4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+// 32-byte streaming load / store (sm_100 and later), as two 16-byte halves.
+__device__ __forceinline__ void ld_stream32(const void *p, uint4 &a, uint4 &b) {
+  asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z),
+                 "=r"(b.w)
                : "l"(p));
-  return v;
 }
-__device__ __forceinline__ void st_stream16(void *p, uint4 v) {
-  asm volatile("st.global.L1::no_allocate.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x),
-               "r"(v.y), "r"(v.z), "r"(v.w)
+__device__ __forceinline__ void st_stream32(void *p, uint4 a, uint4 b) {
+  asm volatile("st.global.L1::no_allocate.v8.u32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
+               "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
                : "memory");
 }
 // Swish derivatives of layer L in HBM, tile-interleaved so that a warp's 32
-// rows of one 16-byte column unit are 512 contiguous bytes (coalesced in
-// both chains): unit (row, chunk jc, unit c16) at
-// (((row / 128) * (W / 64) + jc) * 8 + c16) * 2048 + (row % 128) * 16.
+// rows of one 32-byte column unit (16 columns) are 1 KB contiguous
+// (coalesced in both chains): unit (row, chunk jc, unit m) at
+// (((row / 128) * (W / 64) + jc) * 4 + m) * 4096 + (row % 128) * 32.
 __device__ __forceinline__ uint8_t *gact_unit(const ChainArgs &p, int L, long long row, int jc,
-                                              int c16) {
+                                              int m) {
   return reinterpret_cast<uint8_t *>(p.gact[L]) +
-         ((((row >> 7) * (p.W / 64) + jc) * 8 + c16) << 11) + ((row & 127) << 4);
+         ((((row >> 7) * (p.W / 64) + jc) * 4 + m) << 12) + ((row & 127) << 5);
+}
+// The 64 derivatives of chunk jc of a row (zeros if not live): 16-byte
+// column unit c16 in g[c16].
+__device__ __forceinline__ void load_gact(const ChainArgs &p, int L, long long row, int jc,
+                                          bool live, uint4 (&g)[8]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    if (live)
+      ld_stream32(gact_unit(p, L, row, jc, m), g[2 * m], g[2 * m + 1]);
+    else
+      g[2 * m] = g[2 * m + 1] = make_uint4(0, 0, 0, 0);
+  }
 }
 
 // ReLU bits of layer L in HBM, tile-interleaved the same way: the two
@@ -516,9 +528,10 @@ __device__ __forceinline__ void swish_group(const ChainArgs &p, uint8_t *A, int 
         make_uint4(wh[4 * u], wh[4 * u + 1], wh[4 * u + 2], wh[4 * u + 3]);
   if (gbase) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      st_stream16(gbase + ((size_t)(jc * 8 + 4 * hh + u) << 11),
-                  make_uint4(wg[4 * u], wg[4 * u + 1], wg[4 * u + 2], wg[4 * u + 3]));
+    for (int v = 0; v < 2; ++v)
+      st_stream32(gbase + ((size_t)(jc * 4 + 2 * hh + v) << 12),
+                  make_uint4(wg[8 * v], wg[8 * v + 1], wg[8 * v + 2], wg[8 * v + 3]),
+                  make_uint4(wg[8 * v + 4], wg[8 * v + 5], wg[8 * v + 6], wg[8 * v + 7]));
   }
 }
 
@@ -530,7 +543,7 @@ __device__ __forceinline__ void swish_layer(const ChainArgs &p, uint8_t *A, int 
                                             bool last, int half, float &dot) {
   const int ng = 2 * ((p.W / 64 - half + 1) / 2);
   if (ng == 0) return;
-  // gact_unit(row, 0, 0) of layer L; unit (jc, c16) is 2048 (8 jc + c16) further
+  // gact_unit(row, 0, 0) of layer L; unit (jc, m) is 4096 (4 jc + m) further
   uint8_t *gbase = live && p.gact[L] ? gact_unit(p, L, row, 0, 0) : nullptr;
   auto col = [&](int g) { return 64 * (half + 2 * (g >> 1)) + 32 * (g & 1); };
   uint32_t ra[32], rb[32];
@@ -709,9 +722,7 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
     for (int jc = half; jc < p.W / 64; jc += kP) {
       uint8_t *chunk = A + (size_t)jc * kChunkBytes;
       uint4 gq[8];  // the chunk's derivatives, all loads in flight together
-#pragma unroll
-      for (int c16 = 0; c16 < 8; ++c16)
-        gq[c16] = live ? ld_stream16(gact_unit(p, p.H - 1, row, jc, c16)) : make_uint4(0, 0, 0, 0);
+      load_gact(p, p.H - 1, row, jc, live, gq);
 #pragma unroll
       for (int c16 = 0; c16 < 8; ++c16) {
         const uint32_t gw[4] = {gq[c16].x, gq[c16].y, gq[c16].z, gq[c16].w};
@@ -756,10 +767,7 @@ __device__ bool bwd_epilogue_swish(const ChainMaps &maps, const ChainArgs &p, co
   const long long row = tile * 128 + r_in;
   const bool live = row < p.ns;
   uint4 gq[8];
-#pragma unroll
-  for (int c16 = 0; c16 < 8; ++c16)
-    gq[c16] = live && half < p.W / 64 ? ld_stream16(gact_unit(p, L - 1, row, half, c16))
-                                      : make_uint4(0, 0, 0, 0);
+  load_gact(p, L - 1, row, half, live && half < p.W / 64, gq);
   if (!warp_wait(&s.tfull[slot], tfull_phase & 1, p.err, 18)) return false;
   tc_fence_after();
   if (lane == 0) bulk_wait_read();
@@ -771,12 +779,7 @@ __device__ bool bwd_epilogue_swish(const ChainMaps &maps, const ChainArgs &p, co
   uint4 gn[8];
   for (int jc = half; jc < p.W / 64; jc += 2) {
     const bool more = jc + 2 < p.W / 64;
-    if (more) {
-#pragma unroll
-      for (int c16 = 0; c16 < 8; ++c16)
-        gn[c16] = live ? ld_stream16(gact_unit(p, L - 1, row, jc + 2, c16))
-                       : make_uint4(0, 0, 0, 0);
-    }
+    if (more) load_gact(p, L - 1, row, jc + 2, live, gn);
     float v[64];
     tmem_ld64(trow + 64 * jc, v);
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
