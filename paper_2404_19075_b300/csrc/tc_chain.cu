@@ -111,6 +111,12 @@ __device__ __forceinline__ float4 ld_keep(const float *p) {
       : "l"(p));
   return v;
 }
+// Eight consecutive floats (32-byte aligned) with the evict_last policy.
+__device__ __forceinline__ void ld_keep8(const float *p, float4 &a, float4 &b) {
+  asm("ld.global.nc.L1::evict_last.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
 __device__ __forceinline__ float4 ld_stream4(const float *p) {
   float4 v;
   asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -604,12 +610,17 @@ __device__ __forceinline__ void tmem_put_bias(const float *bias, uint32_t trow, 
     for (int hh = 0; hh < 2; ++hh) {
       uint32_t r[32];
 #pragma unroll
-      for (int i4 = 0; i4 < 8; ++i4) {
-        const float4 b = ld_keep(bias + 64 * jc + 32 * hh + 4 * i4);
-        r[4 * i4] = __float_as_uint(b.x);
-        r[4 * i4 + 1] = __float_as_uint(b.y);
-        r[4 * i4 + 2] = __float_as_uint(b.z);
-        r[4 * i4 + 3] = __float_as_uint(b.w);
+      for (int i8 = 0; i8 < 4; ++i8) {
+        float4 b0, b1;
+        ld_keep8(bias + 64 * jc + 32 * hh + 8 * i8, b0, b1);
+        r[8 * i8] = __float_as_uint(b0.x);
+        r[8 * i8 + 1] = __float_as_uint(b0.y);
+        r[8 * i8 + 2] = __float_as_uint(b0.z);
+        r[8 * i8 + 3] = __float_as_uint(b0.w);
+        r[8 * i8 + 4] = __float_as_uint(b1.x);
+        r[8 * i8 + 5] = __float_as_uint(b1.y);
+        r[8 * i8 + 6] = __float_as_uint(b1.z);
+        r[8 * i8 + 7] = __float_as_uint(b1.w);
       }
       tmem_st32(trow + 64 * jc + 32 * hh, r);
     }
@@ -726,8 +737,8 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
 #pragma unroll
       for (int c16 = 0; c16 < 8; ++c16) {
         const uint32_t gw[4] = {gq[c16].x, gq[c16].y, gq[c16].z, gq[c16].w};
-        const float4 oa = ld_keep(p.w_out + 64 * jc + 8 * c16);
-        const float4 ob = ld_keep(p.w_out + 64 * jc + 8 * c16 + 4);
+        float4 oa, ob;
+        ld_keep8(p.w_out + 64 * jc + 8 * c16, oa, ob);
         const float o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
         uint32_t w[4];
 #pragma unroll
@@ -744,8 +755,8 @@ __device__ void bwd_prologue(const ChainMaps &maps, const ChainArgs &p, uint8_t 
     uint8_t *chunk = A + (size_t)jc * kChunkBytes;
 #pragma unroll
     for (int c16 = 0; c16 < 8; ++c16) {
-      const float4 oa = ld_keep(p.w_out + 64 * jc + 8 * c16);
-      const float4 ob = ld_keep(p.w_out + 64 * jc + 8 * c16 + 4);
+      float4 oa, ob;
+      ld_keep8(p.w_out + 64 * jc + 8 * c16, oa, ob);
       const float o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
       const uint32_t m = c16 < 4 ? mb.x : mb.y;
       uint32_t w[4];

@@ -484,10 +484,10 @@ bool chain_ok(const dinr_ctx *c) {
   if (!(c->W % 64 == 0 && c->W <= 256 && c->H <= kChainMaxLayers && chain_k0(c) <= 256 && enc &&
         chain_stages(c->W, chain_k0(c)) >= 2))
     return false;
-  // biases and output weights are read as float4
+  // biases and output weights are read eight floats (32 bytes) at a time
   for (int L = 0; L <= c->H; ++L)
-    if (c->offb[L] % 4 != 0) return false;
-  return c->offW[c->H] % 4 == 0;
+    if (c->offb[L] % 8 != 0) return false;
+  return c->offW[c->H] % 8 == 0;
 }
 
 // The fused forward chain over a pass: rays of `src` (or points), encoding
