@@ -57,11 +57,11 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FM
 # the captured launch, applied to each launch's algorithmic bytes.
 _CSRC = "paper_2404_19075_b300/csrc/"
 _CHAIN = {"source": [_CSRC + f for f in ("tc_chain.cu", "tc_chain.cuh", "tc_ptx.cuh")],
-          "sha256_16": "488c6f6b9b814743"}
+          "sha256_16": "37ce18a5cb211c73"}
 TRAFFIC = {"tc_fwd_chain": [dict(_CHAIN, bf16_workload=2,
-                                 bytes_per_sample=(10.563072e6 + 2.508109e9) / 1048576)],
+                                 bytes_per_sample=(11.13856e6 + 2.507795e9) / 1048576)],
            "tc_bwd_chain": [dict(_CHAIN, bf16_workload=2,
-                                 bytes_per_sample=(174.582784e6 + 2.625585e9) / 1048576)],
+                                 bytes_per_sample=(175.556608e6 + 2.624955e9) / 1048576)],
            "tc_dw": [{"ratio_to_algorithmic": (1.074768e9 + 5.895424e6) / (2 * 1048576 * 256 * 2),
                       "bf16_workload": 2,
                       "source": [_CSRC + f for f in ("tc_gemm.cu", "tc_gemm.cuh", "tc_ptx.cuh",
