@@ -267,6 +267,11 @@ __device__ __forceinline__ float swish_grad(float z) {
   return s * (1.0f + z * (1.0f - s));
 }
 
+// kEpi, kAct (ReLU 0, Swish 1) and kFp8 are fixed per kernel, so that an
+// epilogue carries no work of the other kinds (a runtime switch left the
+// Swish and FP8 arithmetic in the BF16 ReLU epilogue: 13 % of the wide
+// network's forward GEMM time).
+template <int kEpi, int kAct, bool kFp8>
 __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
                          const CUtensorMap *tout) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -288,22 +293,22 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
     const bool live = row < p.M;
     // prefetch the mask operand of this warp's first chunk
     uint4 hcur[4], hnext[4];
-    if (p.epi == kTcDx && live && half < n_chunks)
+    if (kEpi == kTcDx && live && half < n_chunks)
       load_h32(p.hprev + (long long)row * p.ldh + n0 + half * 32, hcur);
     if (!warp_wait(&s.tfull[ab], ar & 1, p.err, 5)) return;
     tc_fence_after();
     const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)acc_stride(p);
     float dot = 0.0f;
-    const float descale = p.fp8 ? *p.scale_a * *p.scale_b : 1.0f;
-    const float inv_out = p.out8 ? 1.0f / *p.scale_out : 0.0f;
+    const float descale = kFp8 ? *p.scale_a * *p.scale_b : 1.0f;
+    const float inv_out = kFp8 && p.out8 ? 1.0f / *p.scale_out : 0.0f;
     float amax = 0.0f;
     for (int ch = half; ch < n_chunks; ch += 2) {
       const int c0 = n0 + ch * 32;  // output column of the chunk
-      if (p.epi == kTcDx && live && ch + 2 < n_chunks)
+      if (kEpi == kTcDx && live && ch + 2 < n_chunks)
         load_h32(p.hprev + (long long)row * p.ldh + c0 + 64, hnext);
       // forward: the chunk's bias first, so that its load overlaps the TMEM load
       float4 bb[8];
-      if (p.epi == kTcFwd) {
+      if (kEpi == kTcFwd) {
         const float4 *b4 = reinterpret_cast<const float4 *>(p.bias + c0);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -312,7 +317,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
       float v[32];
       tmem_ld32(trow + ch * 32, v);
       if (live) {
-        if (p.epi == kTcFwd) {
+        if (kEpi == kTcFwd) {
           // z = descale * acc + bias; x = act(z). Swish uses a fast
           // exponential and reciprocal (relative error about 1e-6, far below
           // the BF16 rounding of x).
@@ -322,9 +327,9 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
             const float4 b = bb[i / 4];
             const float bi = (i & 3) == 0 ? b.x : (i & 3) == 1 ? b.y : (i & 3) == 2 ? b.z : b.w;
             const float z = fmaf(v[i], descale, bi);
-            x[i] = p.act ? z * __frcp_rn(1.0f + __expf(-z)) : fmaxf(z, 0.0f);
+            x[i] = kAct ? z * __frcp_rn(1.0f + __expf(-z)) : fmaxf(z, 0.0f);
             v[i] = z;
-            amax = fmaxf(amax, fabsf(x[i]));
+            if (kFp8) amax = fmaxf(amax, fabsf(x[i]));
           }
           if (p.w_out) {
 #pragma unroll
@@ -342,7 +347,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
           }
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = x[i];
-          if (p.out8 && c0 + 32 <= p.n_store) {
+          if (kFp8 && p.out8 && c0 + 32 <= p.n_store) {
             uint32_t q8[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j)
@@ -352,13 +357,13 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
             o8[0] = make_uint4(q8[0], q8[1], q8[2], q8[3]);
             o8[1] = make_uint4(q8[4], q8[5], q8[6], q8[7]);
           }
-        } else if (p.epi == kTcDx) {
+        } else if (kEpi == kTcDx) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             uint32_t w[4] = {hcur[j].x, hcur[j].y, hcur[j].z, hcur[j].w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              if (p.act) {
+              if (kAct) {
                 v[8 * j + 2 * e] *= swish_grad(__uint_as_float(w[e] << 16));
                 v[8 * j + 2 * e + 1] *= swish_grad(__uint_as_float(w[e] & 0xFFFF0000u));
               } else {
@@ -368,7 +373,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
             }
           }
         }
-        if ((p.epi == kTcFwd || p.epi == kTcDx) && !p.stage_out) {
+        if ((kEpi == kTcFwd || kEpi == kTcDx) && !p.stage_out) {
           if (c0 + 32 <= p.n_store) {
             uint4 *o = reinterpret_cast<uint4 *>(p.out + (long long)row * p.ldo + c0);
 #pragma unroll
@@ -381,7 +386,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
             for (int i = 0; i < 32 && c0 + i < p.n_store; ++i)
               p.out[(long long)row * p.ldo + c0 + i] = __float2bfloat16_rn(v[i]);
           }
-        } else if (p.epi == kTcDw) {
+        } else if (kEpi == kTcDw) {
           float *o = p.part + ((long long)sp * p.M + row) * p.part_ld + c0;
           for (int i = 0; i < 32 && c0 + i < p.n_store; ++i) o[i] = v[i];
         }
@@ -408,22 +413,22 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
           bulk_commit();
         }
       }
-      if (p.epi == kTcDx) {
+      if (kEpi == kTcDx) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) hcur[j] = hnext[j];
       }
     }
-    if (p.amax) {
+    if (kFp8 && p.amax) {
       // activations are non-negative: their float bits order like integers
       const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
       if (lane == 0 && m != 0u) atomicMax(p.amax, m);
     }
-    if (p.epi == kTcDw && p.with_db && nt == 0 && half == 0) {
+    if (kEpi == kTcDw && p.with_db && nt == 0 && half == 0) {
       float v[32];
       tmem_ld32(trow + p.N, v);  // 16 db columns (all equal) + padding
       if (live) p.part_db[(long long)sp * p.M + row] = v[0];
     }
-    if (p.epi == kTcFwd && p.z_out) {
+    if (kEpi == kTcFwd && p.z_out) {
       // the second half hands its partial dot products to the first half
       float *db = s.dot + (ab & 1) * 256;
       if (half == 1) {
@@ -455,7 +460,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
 }
 
 // The body of both kernels (kPair: a cluster of two CTAs, see the header).
-template <bool kPair>
+template <bool kPair, int kEpi, int kAct, bool kFp8>
 __device__ __forceinline__ void gemm_cta(const CUtensorMap *ta, const CUtensorMap *tb,
                                          const CUtensorMap *tout, const TcGemmArgs &p) {
   extern __shared__ uint8_t smem_raw[];
@@ -505,7 +510,7 @@ __device__ __forceinline__ void gemm_cta(const CUtensorMap *ta, const CUtensorMa
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) mma_issuer<kPair>(p, s, tbase);
   } else {
-    epilogue(p, s, tbase, tout);
+    epilogue<kEpi, kAct, kFp8>(p, s, tbase, tout);
   }
   tc_fence_before();
   __syncthreads();
@@ -519,16 +524,17 @@ __device__ __forceinline__ void gemm_cta(const CUtensorMap *ta, const CUtensorMa
   }
 }
 
+template <int kEpi, int kAct, bool kFp8>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
               const __grid_constant__ CUtensorMap tout, const TcGemmArgs p) {
-  gemm_cta<false>(&ta, &tb, &tout, p);
+  gemm_cta<false, kEpi, kAct, kFp8>(&ta, &tb, &tout, p);
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_tc_gemm_pair(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
                    const __grid_constant__ CUtensorMap tout, const TcGemmArgs p) {
-  gemm_cta<true>(&ta, &tb, &tout, p);
+  gemm_cta<true, kTcDw, 0, false>(&ta, &tb, &tout, p);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -587,6 +593,16 @@ bool make_tmap_bf16_plain(CUtensorMap *tm, const void *ptr, long long rows, long
   return r == CUDA_SUCCESS;
 }
 
+template <int kEpi, int kAct, bool kFp8>
+static int launch_one(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &tout,
+                      const TcGemmArgs &a, int grid, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<kEpi, kAct, kFp8>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  k_tc_gemm<kEpi, kAct, kFp8><<<grid, kThreads, smem, st>>>(ta, tb, tout, a);
+  return (int)cudaGetLastError();
+}
+
 int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap *tout,
                    TcGemmArgs a, int num_sms, cudaStream_t st) {
   if (a.stage_out && (!tout || a.epi == kTcDw || a.n_store % 32 != 0))
@@ -633,13 +649,19 @@ int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorM
     k_tc_gemm_pair<<<2 * clusters, kThreads, smem, st>>>(ta, tb, tout ? *tout : none, a);
     return (int)cudaGetLastError();
   }
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return (int)e;
   int tiles = a.m_tiles * (a.n_tn > 1 ? a.n_tn : 1) * a.splits;
   int grid = tiles < num_sms ? tiles : num_sms;
-  k_tc_gemm<<<grid, kThreads, smem, st>>>(ta, tb, tout ? *tout : none, a);
-  return (int)cudaGetLastError();
+  const CUtensorMap &to = tout ? *tout : none;
+  if (a.epi == kTcDw) return launch_one<kTcDw, 0, false>(ta, tb, to, a, grid, smem, st);
+  if (a.epi == kTcDx)
+    return a.act ? launch_one<kTcDx, 1, false>(ta, tb, to, a, grid, smem, st)
+                 : launch_one<kTcDx, 0, false>(ta, tb, to, a, grid, smem, st);
+  if (a.epi != kTcFwd) return (int)cudaErrorInvalidValue;
+  if (a.fp8)
+    return a.act ? launch_one<kTcFwd, 1, true>(ta, tb, to, a, grid, smem, st)
+                 : launch_one<kTcFwd, 0, true>(ta, tb, to, a, grid, smem, st);
+  return a.act ? launch_one<kTcFwd, 1, false>(ta, tb, to, a, grid, smem, st)
+               : launch_one<kTcFwd, 0, false>(ta, tb, to, a, grid, smem, st);
 }
 
 }  // namespace dinr
