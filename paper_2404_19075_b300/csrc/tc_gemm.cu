@@ -111,6 +111,19 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
+// BF16 pair (lo, hi) of max(x, 0), rounded to nearest even.
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// 0xFFFF in each half of a BF16 pair whose value is > 0.
+__device__ __forceinline__ uint32_t bf16x2_positive(uint32_t w) {
+  uint32_t m;
+  asm("set.gt.u32.bf16x2 %0, %1, %2;" : "=r"(m) : "r"(w), "r"(0u));
+  return m;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t *>(&v);
@@ -316,6 +329,13 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
       }
       float v[32];
       tmem_ld32(trow + ch * 32, v);
+      // the chunk's BF16 output pairs (forward and input gradients; rows past
+      // M stay zero and are clipped by the staged store's tensor map)
+      uint32_t ow[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) ow[k] = 0u;
+      // BF16 ReLU forward: z stays in v and the ReLU is taken in the packing
+      constexpr bool kReluPack = kEpi == kTcFwd && kAct == 0 && !kFp8;
       if (live) {
         if (kEpi == kTcFwd) {
           // z = descale * acc + bias; x = act(z). Swish uses a fast
@@ -326,7 +346,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
           for (int i = 0; i < 32; ++i) {
             const float4 b = bb[i / 4];
             const float bi = (i & 3) == 0 ? b.x : (i & 3) == 1 ? b.y : (i & 3) == 2 ? b.z : b.w;
-            const float z = fmaf(v[i], descale, bi);
+            const float z = kFp8 ? fmaf(v[i], descale, bi) : v[i] + bi;
             x[i] = kAct ? z * __frcp_rn(1.0f + __expf(-z)) : fmaxf(z, 0.0f);
             v[i] = z;
             if (kFp8) amax = fmaxf(amax, fabsf(x[i]));
@@ -336,7 +356,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
             for (int i = 0; i < 32; ++i)
               if (c0 + i < p.n_store) dot = fmaf(x[i], __ldg(p.w_out + c0 + i), dot);
           }
-          if (p.zpre && c0 + 32 <= p.n_store) {
+          if (kAct && p.zpre && c0 + 32 <= p.n_store) {
             uint4 *oz = reinterpret_cast<uint4 *>(p.zpre + (long long)row * p.ldz + c0);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -345,8 +365,10 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
                                  pack_bf16(v[8 * j + 4], v[8 * j + 5]),
                                  pack_bf16(v[8 * j + 6], v[8 * j + 7]));
           }
+          if (!kReluPack) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = x[i];
+            for (int i = 0; i < 32; ++i) v[i] = x[i];
+          }
           if (kFp8 && p.out8 && c0 + 32 <= p.n_store) {
             uint32_t q8[8];
 #pragma unroll
@@ -357,6 +379,10 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
             o8[0] = make_uint4(q8[0], q8[1], q8[2], q8[3]);
             o8[1] = make_uint4(q8[4], q8[5], q8[6], q8[7]);
           }
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            ow[k] = kReluPack ? pack_bf16_relu(v[2 * k], v[2 * k + 1])
+                              : pack_bf16(v[2 * k], v[2 * k + 1]);
         } else if (kEpi == kTcDx) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
@@ -364,11 +390,13 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               if (kAct) {
-                v[8 * j + 2 * e] *= swish_grad(__uint_as_float(w[e] << 16));
-                v[8 * j + 2 * e + 1] *= swish_grad(__uint_as_float(w[e] & 0xFFFF0000u));
+                ow[4 * j + e] =
+                    pack_bf16(v[8 * j + 2 * e] * swish_grad(__uint_as_float(w[e] << 16)),
+                              v[8 * j + 2 * e + 1] * swish_grad(__uint_as_float(w[e] & 0xFFFF0000u)));
               } else {
-                if (!bf16_positive(w[e] & 0xFFFFu)) v[8 * j + 2 * e] = 0.0f;
-                if (!bf16_positive(w[e] >> 16)) v[8 * j + 2 * e + 1] = 0.0f;
+                // the ReLU mask of the pair from one packed compare
+                ow[4 * j + e] = pack_bf16(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]) &
+                                bf16x2_positive(w[e]);
               }
             }
           }
@@ -378,13 +406,11 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
             uint4 *o = reinterpret_cast<uint4 *>(p.out + (long long)row * p.ldo + c0);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-              o[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]),
-                                pack_bf16(v[8 * j + 2], v[8 * j + 3]),
-                                pack_bf16(v[8 * j + 4], v[8 * j + 5]),
-                                pack_bf16(v[8 * j + 6], v[8 * j + 7]));
+              o[j] = make_uint4(ow[4 * j], ow[4 * j + 1], ow[4 * j + 2], ow[4 * j + 3]);
           } else {
+            uint16_t *o = reinterpret_cast<uint16_t *>(p.out + (long long)row * p.ldo + c0);
             for (int i = 0; i < 32 && c0 + i < p.n_store; ++i)
-              p.out[(long long)row * p.ldo + c0 + i] = __float2bfloat16_rn(v[i]);
+              o[i] = (uint16_t)(ow[i >> 1] >> (16 * (i & 1)));
           }
         } else if (kEpi == kTcDw) {
           float *o = p.part + ((long long)sp * p.M + row) * p.part_ld + c0;
@@ -401,10 +427,7 @@ __device__ void epilogue(const TcGemmArgs &p, const Smem &s, uint32_t tbase,
         uint4 *o = reinterpret_cast<uint4 *>(stg + lane * 64);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          o[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]),
-                            pack_bf16(v[8 * j + 2], v[8 * j + 3]),
-                            pack_bf16(v[8 * j + 4], v[8 * j + 5]),
-                            pack_bf16(v[8 * j + 6], v[8 * j + 7]));
+          o[j] = make_uint4(ow[4 * j], ow[4 * j + 1], ow[4 * j + 2], ow[4 * j + 3]);
         fence_async_smem();
         __syncwarp();
         const int row0 = mt * BM + q * 32;
