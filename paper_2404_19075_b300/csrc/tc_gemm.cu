@@ -93,10 +93,19 @@ __device__ __forceinline__ int tile_stride(const TcGemmArgs &p) {
 __device__ __forceinline__ void tile_range(const TcGemmArgs &p, int t, int &mt, int &nt, int &sp,
                                            long long &k0, int &nk, int rank = 0) {
   const int mu = m_units(p);
-  mt = p.pair ? 2 * (t % mu) + rank : t % mu;
-  const int rest = t / mu;
-  nt = rest % n_tn(p);
-  sp = rest / n_tn(p);
+  if (p.splits <= 1 && !p.pair) {
+    // no K split (forward, input gradients): the N tiles of one M tile are
+    // consecutive, so CTAs that run at the same time read the same rows of
+    // A, which then come from HBM once and from L2 for the other N tiles
+    nt = t % n_tn(p);
+    mt = t / n_tn(p);
+    sp = 0;
+  } else {
+    mt = p.pair ? 2 * (t % mu) + rank : t % mu;
+    const int rest = t / mu;
+    nt = rest % n_tn(p);
+    sp = rest / n_tn(p);
+  }
   k0 = (long long)sp * p.k_per_split;
   long long k1 = k0 + p.k_per_split < p.K ? k0 + p.k_per_split : p.K;
   const int bk = p.fp8 ? 2 * BK : BK;  // K elements per 128-byte swizzled row
