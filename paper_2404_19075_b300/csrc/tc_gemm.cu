@@ -93,12 +93,13 @@ __device__ __forceinline__ int tile_stride(const TcGemmArgs &p) {
 __device__ __forceinline__ void tile_range(const TcGemmArgs &p, int t, int &mt, int &nt, int &sp,
                                            long long &k0, int &nk, int rank = 0) {
   const int mu = m_units(p);
-  if (p.splits <= 1 && !p.pair) {
-    // no K split (forward, input gradients): the N tiles of one M tile are
-    // consecutive, so CTAs that run at the same time read the same rows of
-    // A, which then come from HBM once and from L2 for the other N tiles
+  if (p.splits <= 1) {
+    // no K split (forward, input gradients): the N tiles of one M tile (or
+    // pair of M tiles) are consecutive, so CTAs that run at the same time
+    // read the same rows of A, which then come from HBM once and from L2
+    // for the other N tiles
     nt = t % n_tn(p);
-    mt = t / n_tn(p);
+    mt = p.pair ? 2 * (t / n_tn(p)) + rank : t / n_tn(p);
     sp = 0;
   } else {
     mt = p.pair ? 2 * (t % mu) + rank : t % mu;
@@ -166,12 +167,19 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
         // the bytes of both (its MMA thread reads both halves)
         if (rank == 0) mbar_expect_tx(&s.full[st], 2 * tx);
         const uint32_t bar = mapa_shared(smem_u32(&s.full[st]), 0);
-        // (pair mode: MN-major A and B) this CTA's 128 columns of delta and
-        // its half of the N columns of h
-        tma_load_2d_pair(ta, bar, da, mt * BM, kx);
-        tma_load_2d_pair(ta, bar, da + 8192, mt * BM + 64, kx);
-        for (uint32_t j = 0; j < nb_mn; ++j)
-          tma_load_2d_pair(tb, bar, db + 8192 * j, n0 + 64 * (int)j, kx);
+        // this CTA's 128 rows of A and its half of the N rows of B
+        if (!p.a_mn) {
+          tma_load_2d_pair(ta, bar, da, kx, mt * BM);
+        } else {
+          tma_load_2d_pair(ta, bar, da, mt * BM, kx);
+          tma_load_2d_pair(ta, bar, da + 8192, mt * BM + 64, kx);
+        }
+        if (!p.b_mn) {
+          tma_load_2d_pair(tb, bar, db, kx, n0);
+        } else {
+          for (uint32_t j = 0; j < nb_mn; ++j)
+            tma_load_2d_pair(tb, bar, db + 8192 * j, n0 + 64 * (int)j, kx);
+        }
         continue;
       }
       mbar_expect_tx(&s.full[st], tx);
@@ -563,10 +571,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   gemm_cta<false, kEpi, kAct, kFp8>(&ta, &tb, &tout, p);
 }
 
+template <int kEpi, int kAct>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_tc_gemm_pair(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
                    const __grid_constant__ CUtensorMap tout, const TcGemmArgs p) {
-  gemm_cta<true, kTcDw, 0, false>(&ta, &tb, &tout, p);
+  gemm_cta<true, kEpi, kAct, false>(&ta, &tb, &tout, p);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -635,20 +644,50 @@ static int launch_one(const CUtensorMap &ta, const CUtensorMap &tb, const CUtens
   return (int)cudaGetLastError();
 }
 
+// The same on clusters of two CTAs: as many clusters as can be resident at
+// once (a persistent launch with clusters that would wait for others to
+// finish runs a tail); if the query fails, one per SM pair (extra clusters
+// then run in a later wave, which costs time but nothing else).
+template <int kEpi, int kAct>
+static int launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &tout,
+                       const TcGemmArgs &a, int num_sms, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_pair<kEpi, kAct>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * (num_sms / 2), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  int max_clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&max_clusters, k_tc_gemm_pair<kEpi, kAct>, &cfg) !=
+          cudaSuccess ||
+      max_clusters < 1) {
+    cudaGetLastError();
+    max_clusters = num_sms / 2 > 0 ? num_sms / 2 : 1;
+  }
+  const int pair_tiles = (a.m_tiles + 1) / 2 * (a.n_tn > 1 ? a.n_tn : 1) * a.splits;
+  const int clusters = pair_tiles < max_clusters ? pair_tiles : max_clusters;
+  k_tc_gemm_pair<kEpi, kAct><<<2 * clusters, kThreads, smem, st>>>(ta, tb, tout, a);
+  return (int)cudaGetLastError();
+}
+
 int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap *tout,
                    TcGemmArgs a, int num_sms, cudaStream_t st) {
   if (a.stage_out && (!tout || a.epi == kTcDw || a.n_store % 32 != 0))
     return (int)cudaErrorInvalidValue;
   if (a.fp8 && (a.epi != kTcFwd || a.a_mn || a.b_mn || a.with_db))
     return (int)cudaErrorInvalidValue;
-  // pair mode: weight gradients only (MN-major operands), an even number of
-  // 128-row M tiles and each CTA's half of N a whole number of 64-column boxes
-  if (a.pair && (a.epi != kTcDw || a.fp8 || !a.a_mn || !a.b_mn || a.m_tiles % 2 != 0 ||
-                 (a.N != 128 && a.N != 256)))
+  // pair mode: BF16, an even number of 128-row M tiles; weight gradients
+  // (MN-major A and B, each CTA's half of N a whole number of 64-column
+  // boxes) or forward / input gradients (K-major A and B, N = 256)
+  if (a.pair && (a.fp8 || a.m_tiles % 2 != 0 ||
+                 (a.epi == kTcDw ? (!a.a_mn || !a.b_mn || (a.N != 128 && a.N != 256))
+                                 : (a.a_mn || a.b_mn || a.N != 256))))
     return (int)cudaErrorInvalidValue;
   a.a_bytes = BM * BK * 2;  // 128 rows x 128 bytes, or 2 MN-major boxes of 64 x 128 bytes
   // MN-major B: 64-column boxes of 64 x 128 bytes (a pair CTA holds half of N)
-  a.b_bytes = a.b_mn ? (((a.pair ? a.N / 2 : a.N) + 63) / 64) * 8192 : a.N * BK * 2;
+  a.b_bytes = a.b_mn ? (((a.pair ? a.N / 2 : a.N) + 63) / 64) * 8192
+                      : (a.pair ? a.N / 2 : a.N) * BK * 2;
   const int fixed = kOnesBytes + 2048 /*dot buffer*/ + 1024 /*alignment*/ + 256 /*barriers*/ +
                     (a.stage_out ? kEpiWarps * 2 * kStageBytes : 0);
   const int budget = 220 * 1024;
@@ -658,32 +697,17 @@ int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorM
   size_t smem = (size_t)a.stages * (a.a_bytes + a.b_bytes) + fixed;
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
+  const CUtensorMap &to = tout ? *tout : none;
   if (a.pair) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_pair,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    // as many clusters as can be resident at once (a persistent launch
-    // with clusters that would wait for others to finish runs a tail); if
-    // the query fails, one per SM pair (extra clusters then run in a later
-    // wave, which costs time but nothing else)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * (num_sms / 2), 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    int max_clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&max_clusters, k_tc_gemm_pair, &cfg) != cudaSuccess ||
-        max_clusters < 1) {
-      cudaGetLastError();
-      max_clusters = num_sms / 2 > 0 ? num_sms / 2 : 1;
-    }
-    const int pair_tiles = (a.m_tiles + 1) / 2 * (a.n_tn > 1 ? a.n_tn : 1) * a.splits;
-    const int clusters = pair_tiles < max_clusters ? pair_tiles : max_clusters;
-    k_tc_gemm_pair<<<2 * clusters, kThreads, smem, st>>>(ta, tb, tout ? *tout : none, a);
-    return (int)cudaGetLastError();
+    if (a.epi == kTcDw) return launch_pair<kTcDw, 0>(ta, tb, to, a, num_sms, smem, st);
+    if (a.epi == kTcDx)
+      return a.act ? launch_pair<kTcDx, 1>(ta, tb, to, a, num_sms, smem, st)
+                   : launch_pair<kTcDx, 0>(ta, tb, to, a, num_sms, smem, st);
+    return a.act ? launch_pair<kTcFwd, 1>(ta, tb, to, a, num_sms, smem, st)
+                 : launch_pair<kTcFwd, 0>(ta, tb, to, a, num_sms, smem, st);
   }
   int tiles = a.m_tiles * (a.n_tn > 1 ? a.n_tn : 1) * a.splits;
   int grid = tiles < num_sms ? tiles : num_sms;
-  const CUtensorMap &to = tout ? *tout : none;
   if (a.epi == kTcDw) return launch_one<kTcDw, 0, false>(ta, tb, to, a, grid, smem, st);
   if (a.epi == kTcDx)
     return a.act ? launch_one<kTcDx, 1, false>(ta, tb, to, a, grid, smem, st)

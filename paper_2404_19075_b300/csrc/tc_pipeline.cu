@@ -294,7 +294,7 @@ dinr_status gemm(dinr_ctx *c, const char *name, double flops, double bytes, TcGe
                  long long b_rows, long long b_cols) {
   CUtensorMap ta, tb;
   int a_box = a.a_mn ? 64 : 128;
-  int b_box = a.b_mn ? 64 : a.N;
+  int b_box = a.b_mn ? 64 : (a.pair ? a.N / 2 : a.N);  // a pair CTA loads half of N
   if (!make_tmap_bf16(&ta, A, a_rows, a_cols, a_cols, a_box) ||
       !make_tmap_bf16(&tb, B, b_rows, b_cols, b_cols, b_box))
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "tensor map encoding failed (%s)", name);
@@ -315,6 +315,13 @@ dinr_status gemm(dinr_ctx *c, const char *name, double flops, double bytes, TcGe
 
 // N tiles of a W-wide output: one tile up to 256 columns, else 256-wide tiles.
 int tile_w(int W) { return W <= 256 ? W : 256; }
+
+// Forward / input-gradient GEMMs on two-SM tiles (256 rows over a CTA pair,
+// each SM loading half of the weight rows): BF16, 256-column N tiles and an
+// even number of 128-row M tiles.
+static bool pair_ok(const TcGemmArgs &a) {
+  return !a.fp8 && a.N == 256 && a.m_tiles % 2 == 0 && !a.a_mn && !a.b_mn;
+}
 int tiles_n(int W) { return W <= 256 ? 1 : W / 256; }
 
 // Activation buffers of the unfused path. Without recomputation layer L has
@@ -432,6 +439,7 @@ dinr_status forward_layers(dinr_ctx *c, long long ns, int L0, int L1) {
                 ns * (acols + 3.0 * c->W), a, A8, ns, acols, t->W8[L], c->W, t->kpad[L]);
     } else {
       const void *A = L == 0 ? (const void *)t->E : (const void *)hid(c, L - 1, ns);
+      a.pair = pair_ok(a) ? 1 : 0;
       s = gemm(c, L0 > 0 || L1 < c->H ? "tc_fwd_recompute" : "tc_fwd",
                2.0 * ns * c->W * c->fan_in[L], 2.0 * ns * (acols + c->W), a, A, ns, acols,
                t->Wb[L], c->W, t->kpad[L]);
@@ -703,6 +711,7 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
       b.act = swish ? 1 : 0;
       b.hprev = swish ? zid(c, L - 1, ns) : hid(c, L - 1, ns);
       b.ldh = W;
+      b.pair = pair_ok(b) ? 1 : 0;
       s = gemm(c, "tc_dx", 2.0 * ns * W * W, 2.0 * ns * 3 * W, b, D, ns, W, t->WbT[L], W, W);
       if (s != DINR_OK) return s;
       __nv_bfloat16 *tmp = D;
