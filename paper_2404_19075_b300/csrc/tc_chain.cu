@@ -383,7 +383,10 @@ __device__ __forceinline__ void write_features(uint8_t *A, const float (&c)[4], 
         if ((l & 3) == 0) {
           const float x = hi * scale;
           const float y = x - 2.0f * rintf(0.5f * x);
-          sincospif(y, &sp, &cp);
+          // the hardware sine and cosine of pi y, |y| <= 1 (absolute error
+          // about 1e-6, at most about 1e-5 after three doublings; BF16
+          // resolution is 4e-3 relative)
+          __sincosf(3.14159265358979f * y, &sp, &cp);
         } else {
           const float s2 = 2.0f * sp * cp;
           cp = (cp - sp) * (cp + sp);
@@ -454,8 +457,9 @@ __device__ __forceinline__ void tile_features(const ChainArgs &p, uint8_t *A, lo
 // Layer-0 input of one tile: the Fourier features of its 128 samples, in
 // the K-chunks this warp owns (chunks half, half + 2, ...). F is a template
 // parameter so that every feature lands in a register by static index.
-// Octave features use exact sincospif at octaves 0, 4, 8, ... and angle
-// doubling in between (error about 1e-6, far below BF16 resolution).
+// Octave features use the hardware sincos of the reduced phase at octaves
+// 0, 4, 8, ... and angle doubling in between (error below about 1e-5, far
+// below BF16 resolution).
 template <int F>
 __device__ void encode_tile(const ChainMaps &maps, const ChainArgs &p, uint8_t *A,
                             long long tile, int q, int half, int lane) {
