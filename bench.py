@@ -57,16 +57,16 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FM
 # the captured launch, applied to each launch's algorithmic bytes.
 _CSRC = "paper_2404_19075_b300/csrc/"
 _CHAIN = {"source": [_CSRC + f for f in ("tc_chain.cu", "tc_chain.cuh", "tc_ptx.cuh")],
-          "sha256_16": "37ce18a5cb211c73"}
+          "sha256_16": "0b95c887b4baf3b9"}
 TRAFFIC = {"tc_fwd_chain": [dict(_CHAIN, bf16_workload=2,
-                                 bytes_per_sample=(11.13856e6 + 2.507795e9) / 1048576)],
+                                 bytes_per_sample=(10.45888e6 + 2.507943e9) / 1048576)],
            "tc_bwd_chain": [dict(_CHAIN, bf16_workload=2,
-                                 bytes_per_sample=(175.556608e6 + 2.624955e9) / 1048576)],
-           "tc_dw": [{"ratio_to_algorithmic": (1.075108e9 + 5.877248e6) / (2 * 1048576 * 256 * 2),
+                                 bytes_per_sample=(176.600064e6 + 2.624401e9) / 1048576)],
+           "tc_dw": [{"ratio_to_algorithmic": (1.074876e9 + 4.859648e6) / (2 * 1048576 * 256 * 2),
                       "bf16_workload": 2,
                       "source": [_CSRC + f for f in ("tc_gemm.cu", "tc_gemm.cuh", "tc_ptx.cuh",
                                                      "tc_pair.cuh")],
-                      "sha256_16": "d1eae6f6276a5eb8"}]}
+                      "sha256_16": "ef0ab8935cae0d04"}]}
 
 # Kernels without tensor-core work of the method: their roofline is GB/s of
 # algorithmic bytes. Every other BF16 / FP8 kernel is measured against the

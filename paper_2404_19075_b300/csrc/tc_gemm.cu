@@ -109,7 +109,7 @@ __device__ __forceinline__ void tile_range(const TcGemmArgs &p, int t, int &mt, 
   }
   k0 = (long long)sp * p.k_per_split;
   long long k1 = k0 + p.k_per_split < p.K ? k0 + p.k_per_split : p.K;
-  const int bk = p.fp8 ? 2 * BK : BK;  // K elements per 128-byte swizzled row
+  const int bk = tc_k_block(p);
   nk = (int)((k1 - k0 + bk - 1) / bk);
 }
 
@@ -147,6 +147,8 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
   const int S = p.stages;
   const uint32_t nb_mn = (uint32_t)(((kPair ? p.N / 2 : p.N) + 63) / 64);
   const uint32_t tx = (uint32_t)p.a_bytes + (uint32_t)p.b_bytes;
+  const int kblk = tc_k_block(p);
+  const int mn_box = kblk * 128;  // bytes of one 64-column MN-major box
   uint32_t it = 0;
   const int rank = kPair ? (int)cluster_ctarank() : 0;
   const int n_tiles = n_tiles_of(p);
@@ -159,7 +161,7 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
     for (int kb = 0; kb < nk; ++kb, ++it) {
       uint32_t st = it % S, rd = it / S;
       if (!mbar_wait(&s.empty[st], (rd & 1) ^ 1, p.err, 1)) return;
-      int kx = (int)(k0 + (long long)kb * (p.fp8 ? 2 * BK : BK));
+      int kx = (int)(k0 + (long long)kb * kblk);
       uint8_t *da = s.a + (size_t)st * p.a_bytes;
       uint8_t *db = s.b + (size_t)st * p.b_bytes;
       if constexpr (kPair) {
@@ -172,13 +174,13 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
           tma_load_2d_pair(ta, bar, da, kx, mt * BM);
         } else {
           tma_load_2d_pair(ta, bar, da, mt * BM, kx);
-          tma_load_2d_pair(ta, bar, da + 8192, mt * BM + 64, kx);
+          tma_load_2d_pair(ta, bar, da + mn_box, mt * BM + 64, kx);
         }
         if (!p.b_mn) {
           tma_load_2d_pair(tb, bar, db, kx, n0);
         } else {
           for (uint32_t j = 0; j < nb_mn; ++j)
-            tma_load_2d_pair(tb, bar, db + 8192 * j, n0 + 64 * (int)j, kx);
+            tma_load_2d_pair(tb, bar, db + mn_box * j, n0 + 64 * (int)j, kx);
         }
         continue;
       }
@@ -187,13 +189,13 @@ __device__ void producer(const CUtensorMap *ta, const CUtensorMap *tb, const TcG
         tma_load_2d(ta, &s.full[st], da, kx, mt * BM);
       } else {
         tma_load_2d(ta, &s.full[st], da, mt * BM, kx);
-        tma_load_2d(ta, &s.full[st], da + 8192, mt * BM + 64, kx);
+        tma_load_2d(ta, &s.full[st], da + mn_box, mt * BM + 64, kx);
       }
       if (!p.b_mn) {
         tma_load_2d(tb, &s.full[st], db, kx, n0);
       } else {
         for (uint32_t j = 0; j < nb_mn; ++j)
-          tma_load_2d(tb, &s.full[st], db + 8192 * j, n0 + 64 * (int)j, kx);
+          tma_load_2d(tb, &s.full[st], db + mn_box * j, n0 + 64 * (int)j, kx);
       }
     }
   }
@@ -219,6 +221,9 @@ __device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
   const uint32_t idesc_db2 = idesc_bf16(2 * BM, 16, p.a_mn, false);
   // an all-ones 16 x 16 BF16 block, no swizzle: every layout reads ones
   const uint64_t ones = smem_desc(smem_u32(s.ones), 128, 256, 0);
+  // instructions per stage, each over 32 bytes of K (16 BF16 or 32 E4M3)
+  const int n_k16 = p.a_mn ? tc_k_block(p) / 16 : BK / 16;
+  const uint32_t mn_box = (uint32_t)tc_k_block(p) * 128;
   uint32_t it = 0, lt = 0;
   const int n_tiles = n_tiles_of(p);
   bool ok = true;
@@ -241,12 +246,12 @@ __device__ void mma_issuer(const TcGemmArgs &p, const Smem &s, uint32_t tbase) {
       uint32_t aa = smem_u32(s.a + (size_t)st * p.a_bytes);
       uint32_t ba = smem_u32(s.b + (size_t)st * p.b_bytes);
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
+      for (int k = 0; k < n_k16; ++k) {
         // K-major: the next 16 elements of K are 32 bytes further along
         // each swizzled 128-byte row; MN-major: 16 more rows of 128 bytes.
-        uint64_t adesc = p.a_mn ? smem_desc(aa + 2048 * k, 8192, 1024, kSwizzle128)
+        uint64_t adesc = p.a_mn ? smem_desc(aa + 2048 * k, mn_box, 1024, kSwizzle128)
                                 : smem_desc(aa + 32 * k, 16, 1024, kSwizzle128);
-        uint64_t bdesc = p.b_mn ? smem_desc(ba + 2048 * k, 8192, 1024, kSwizzle128)
+        uint64_t bdesc = p.b_mn ? smem_desc(ba + 2048 * k, mn_box, 1024, kSwizzle128)
                                 : smem_desc(ba + 32 * k, 16, 1024, kSwizzle128);
         uint32_t acc = (kb | k) != 0;
         // both kinds take 32 bytes of K per instruction (16 BF16 or 32 E4M3)
@@ -680,13 +685,18 @@ int launch_tc_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorM
   // pair mode: BF16, an even number of 128-row M tiles; weight gradients
   // (MN-major A and B, each CTA's half of N a whole number of 64-column
   // boxes) or forward / input gradients (K-major A and B, N = 256)
+  // an MN-major A sets the stage's K block for both operands
+  if (a.a_mn && !a.b_mn) return (int)cudaErrorInvalidValue;
+  if (a.k_per_split % tc_k_block(a) != 0) return (int)cudaErrorInvalidValue;
   if (a.pair && (a.fp8 || a.m_tiles % 2 != 0 ||
                  (a.epi == kTcDw ? (!a.a_mn || !a.b_mn || (a.N != 128 && a.N != 256))
                                  : (a.a_mn || a.b_mn || a.N != 256))))
     return (int)cudaErrorInvalidValue;
-  a.a_bytes = BM * BK * 2;  // 128 rows x 128 bytes, or 2 MN-major boxes of 64 x 128 bytes
-  // MN-major B: 64-column boxes of 64 x 128 bytes (a pair CTA holds half of N)
-  a.b_bytes = a.b_mn ? (((a.pair ? a.N / 2 : a.N) + 63) / 64) * 8192
+  // MN-major operands come in 64-column boxes of k_block rows x 128 bytes
+  // (a pair CTA holds half of N); K-major ones in rows of 128 bytes
+  const int mn_box = tc_k_block(a) * 128;
+  a.a_bytes = a.a_mn ? 2 * mn_box : BM * BK * 2;
+  a.b_bytes = a.b_mn ? (((a.pair ? a.N / 2 : a.N) + 63) / 64) * mn_box
                       : (a.pair ? a.N / 2 : a.N) * BK * 2;
   const int fixed = kOnesBytes + 2048 /*dot buffer*/ + 1024 /*alignment*/ + 256 /*barriers*/ +
                     (a.stage_out ? kEpiWarps * 2 * kStageBytes : 0);

@@ -30,7 +30,7 @@ struct TcGemmArgs {
   long long K;           // reduction extent
   int a_mn, b_mn;
   int m_tiles, splits;
-  long long k_per_split; // multiple of 64
+  long long k_per_split; // multiple of tc_k_block
   int n_store;           // columns written (<= N * n_tn)
   // kTcFwd
   const float *bias;
@@ -68,12 +68,22 @@ struct TcGemmArgs {
   // launch geometry (filled by the launcher)
   int stages, a_bytes, b_bytes;
   int *err;              // device flag: nonzero when a bounded wait gave up
-  // kTcDw with MN-major A and B only: run on clusters of two CTAs (two SMs)
-  // whose tensor cores share one M = 256 MMA (tcgen05 .cta_group::2); needs
-  // an even m_tiles and N of 128 or 256. Results are bitwise those of the
+  // Run on clusters of two CTAs (two SMs) whose tensor cores share one
+  // M = 256 MMA (tcgen05 .cta_group::2); needs BF16 and an even m_tiles, and
+  // either kTcDw with MN-major A and B and N of 128 or 256, or kTcFwd / kTcDx
+  // with K-major A and B and N = 256. Results are bitwise those of the
   // single-CTA kernel (the same products summed in the same order).
   int pair;
 };
+
+// K elements a pipeline stage holds. K-major operands take one 128-byte
+// swizzled row per M/N row: 64 BF16 or 128 E4M3 values. MN-major operands
+// (the weight gradients, K = samples; A and B both MN-major) take 128 rows
+// of K per stage, which halves the stages per tile and so the barrier round
+// trips between the loader and the MMA issuer. k_per_split is a multiple.
+__host__ __device__ __forceinline__ int tc_k_block(const TcGemmArgs &p) {
+  return p.fp8 || p.a_mn ? 128 : 64;
+}
 
 // 2D BF16 tensor map over a row-major [rows][cols] array with row stride
 // ld (elements), box {64, box_rows}, 128-byte swizzle, zero fill.

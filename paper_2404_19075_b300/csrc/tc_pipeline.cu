@@ -293,8 +293,10 @@ dinr_status gemm(dinr_ctx *c, const char *name, double flops, double bytes, TcGe
                  const void *A, long long a_rows, long long a_cols, const void *B,
                  long long b_rows, long long b_cols) {
   CUtensorMap ta, tb;
-  int a_box = a.a_mn ? 64 : 128;
-  int b_box = a.b_mn ? 64 : (a.pair ? a.N / 2 : a.N);  // a pair CTA loads half of N
+  // MN-major operands: boxes of one stage's K rows; K-major: the tile's
+  // rows (a pair CTA loads half of N)
+  int a_box = a.a_mn ? tc_k_block(a) : 128;
+  int b_box = a.b_mn ? tc_k_block(a) : (a.pair ? a.N / 2 : a.N);
   if (!make_tmap_bf16(&ta, A, a_rows, a_cols, a_cols, a_box) ||
       !make_tmap_bf16(&tb, B, b_rows, b_cols, b_cols, b_box))
     return (dinr_status)dinr_fail(c, DINR_ERR_CUDA, "tensor map encoding failed (%s)", name);
@@ -681,7 +683,7 @@ dinr_status backward(dinr_ctx *c, long long ns, bool acc) {
       if (in_cols <= 128) a.N = 128;
     }
     a.splits = splits_for(ns, a.m_tiles * a.n_tn, t->num_sms);
-    a.k_per_split = ((ns + a.splits - 1) / a.splits + 63) / 64 * 64;
+    a.k_per_split = ((ns + a.splits - 1) / a.splits + 127) / 128 * 128;  // tc_k_block
     a.splits = (int)((ns + a.k_per_split - 1) / a.k_per_split);
     a.n_store = fan_in;
     a.part = t->part;
