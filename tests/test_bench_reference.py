@@ -32,3 +32,18 @@ def test_reference_arm_json_line(monkeypatch):
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_equal_error_time_is_where_the_error_settles():
+    """Time to equal error is taken where a path's error stays at or below
+    the target, not at an early dip (the error of a nearly empty volume)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = [{"step": 50, "rel_l2": 0.94}, {"step": 100, "rel_l2": 1.45},
+         {"step": 150, "rel_l2": 0.80}, {"step": 200, "rel_l2": 0.70},
+         {"step": 250, "rel_l2": 0.69}]
+    assert bench.settled_at(c, 0.70)["step"] == 200
+    assert bench.settled_at(c, 0.95)["step"] == 150
+    assert bench.settled_at(c, 0.60) is None
+    assert bench.settled_at(c, 2.0)["step"] == 50
+    assert bench.settled_at([], 1.0) is None
