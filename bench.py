@@ -653,7 +653,9 @@ def main():
     ap.add_argument("--recompute", type=int, default=0,
                     help="activation recomputation of the unfused BF16 path (0, 1, -1 auto)")
     ap.add_argument("--equal-error-steps", type=int, default=1000,
-                    help="Adam steps of the BF16-vs-FP32 reconstruction comparison (0 skips it)")
+                    help="Adam steps of the FP32 path in the time-to-equal-error comparison "
+                         "(its final error is the target; BF16 runs up to twice as many; "
+                         "0 skips it)")
     ap.add_argument("--equal-error-every", type=int, default=250,
                     help="steps between scorings of the reconstruction in that comparison")
     ap.add_argument("--serve-queries", type=int, default=200,
