@@ -47,3 +47,31 @@ def test_equal_error_time_is_where_the_error_settles():
     assert bench.settled_at(c, 0.60) is None
     assert bench.settled_at(c, 2.0)["step"] == 50
     assert bench.settled_at([], 1.0) is None
+
+
+def test_recorded_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
+    """The DRAM traffic a bench line reports comes from recorded counters
+    only while the kernel's source is the one they were taken on: the
+    current sources hash to the recorded keys, and a changed source (a copy
+    of the tree with one byte more) reports null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for kernel, entries in bench.TRAFFIC.items():
+        for e in entries:
+            assert bench.source_hash(e["source"]) == e["sha256_16"], kernel
+    t = bench.traffic_of("tc_fwd_chain", 2, 1000, 0.0)
+    assert t == bench.TRAFFIC["tc_fwd_chain"][0]["bytes_per_sample"] * 1000
+    assert bench.traffic_of("tc_dw", 2, 0, 1e9) == bench.TRAFFIC["tc_dw"][0][
+        "ratio_to_algorithmic"] * 1e9
+    assert bench.traffic_of("tc_fwd_chain", 3, 1000, 0.0) is None   # no capture for workload 3
+    assert bench.traffic_of("no_such_kernel", 2, 1000, 0.0) is None
+    # a changed source: the same files under a root where one differs
+    import shutil
+    for p in bench.TRAFFIC["tc_fwd_chain"][0]["source"]:
+        dst = tmp_path / p
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(ROOT, p), dst)
+    with open(tmp_path / bench.TRAFFIC["tc_fwd_chain"][0]["source"][0], "ab") as f:
+        f.write(b" ")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_of("tc_fwd_chain", 2, 1000, 0.0) is None
